@@ -1,0 +1,169 @@
+/*
+ * slimsell.h -- C ABI of the GB300 SlimSell BFS library (libslimsell.so).
+ *
+ * BFS as repeated sparse-matrix x dense-vector products over the tropical,
+ * real, boolean and sel-max semirings (Section III-A) on the SlimSell layout
+ * (Section III-B: Sell-C-sigma with the value array dropped and padding
+ * marked by -1 in col), with SlimWork chunk skipping (Section III-C) and
+ * SlimChunk splitting of long chunks (Section III-D).
+ *
+ * Conventions for every entry point:
+ *  - Pointers prefixed d_ are DEVICE pointers on the current CUDA device;
+ *    h_ pointers are host pointers.  Sizes are element counts.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *  - The caller owns every buffer it passes in; the handle owns its layout and
+ *    scratch buffers, which slimsell_destroy frees.
+ *  - Vertex ids are the caller's original ids in [0, n).  Unreached vertices get
+ *    dist = parent = -1; the root gets dist = 0 and parent = root.
+ *  - Parents are canonical: the largest-id neighbour one level closer to the
+ *    root, for every semiring (sel-max yields it directly, the others through
+ *    the DP transformation of Section II-C).  Results do not depend on C, sigma,
+ *    the split width or the iteration variant.
+ *  - Errors: a non-zero ss_status is returned and slimsell_last_error() gives a
+ *    message (thread-local, valid until the next call on that thread).
+ *    Invalid arguments are detected on the host before any work is queued.
+ *  - A handle may be used by one host thread at a time.
+ */
+#ifndef SLIMSELL_H
+#define SLIMSELL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct slimsell_graph* slimsell_handle;
+
+/* Semirings of Section III-A. */
+typedef enum {
+  SS_TROPICAL = 0, /* (R u {inf}, min, +, inf, 0): f_k = x_k = A' (x) f_{k-1}          */
+  SS_REAL = 1,     /* (R, +, *, 0, 1): f_k = x_k (.) g_k; fp32 values (path counts)    */
+  SS_BOOLEAN = 2,  /* ({0,1}, |, &, 0, 1): f_k = x_k & g_k; 1-bit frontier            */
+  SS_SELMAX = 3    /* (R, max, *, -inf, 1): x carries vertex ids; parents come out directly */
+} ss_semiring;
+
+typedef enum {
+  SS_OK = 0,
+  SS_ERR_INVALID = 1,     /* bad argument (checked on the host, nothing queued)  */
+  SS_ERR_OOM = 2,         /* device allocation failed                            */
+  SS_ERR_CUDA = 3,        /* a CUDA call failed; see slimsell_last_error()       */
+  SS_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up                  */
+  SS_ERR_UNSUPPORTED = 5  /* combination not implemented                         */
+} ss_status;
+
+/* Per-iteration schedule (how each frontier expansion is executed; results are
+ * identical for all of them). */
+typedef enum {
+  SS_V_FULL = 0,          /* every chunk, every column (plain BFS-SpMV, Section III-A)        */
+  SS_V_SLIMWORK = 1,      /* skip chunks whose rows are all visited (SlimWork, Section III-C) */
+  SS_V_PUSH = 2,          /* compacted-frontier push (work-avoidance variant, Section V)      */
+  SS_V_PULL_FILTERED = 3, /* pull over unvisited rows only, stopping at the first hit         */
+  SS_V_HEURISTIC = 4,     /* per-iteration choice by a frontier-size rule                      */
+  SS_V_LEARNED = 5        /* per-iteration choice by the loaded selector MLP                   */
+} ss_policy;
+
+/* Layout summary of a built handle. */
+typedef struct {
+  int32_t n, C, sigma, split_w;
+  int32_t n_chunks;        /* ceil(n / C)                                             */
+  int32_t n_items;         /* work items after SlimChunk splitting                    */
+  int32_t n_split_chunks;  /* chunks with cl > split_w                                */
+  int32_t max_degree;
+  int64_t nnz;             /* directed nonzeros of the input CSR                      */
+  int64_t slots;           /* |col| = sum_i C * cl_i = nnz + P                        */
+  int64_t padding;         /* P                                                       */
+  int64_t device_bytes;    /* bytes the handle holds on the device                    */
+} ss_info;
+
+/* One frontier expansion (iteration k discovers the vertices at distance k). */
+typedef struct {
+  int64_t frontier;        /* vertices discovered in this iteration                   */
+  int64_t frontier_degree; /* sum of their degrees                                    */
+  int64_t slots;           /* col slots read by the iteration kernels                 */
+  int64_t active_chunks;   /* chunks processed (not skipped)                          */
+  int32_t variant;         /* ss_policy value actually executed (0..3)                */
+  int32_t reserved;
+} ss_iter_stats;
+
+/* Summary of the last slimsell_bfs call on a handle. */
+typedef struct {
+  int32_t iterations;      /* SpMV passes, including the final one that adds nothing */
+  int32_t semiring;
+  int64_t reached;         /* vertices with a finite distance                         */
+  int64_t reached_degree;  /* sum of their degrees = 2 * edges in the component       */
+  int64_t slots;           /* total col slots read                                    */
+  int64_t dp_slots;        /* col slots read by the DP pass (0 for sel-max)           */
+  double iter_kernel_ms;   /* CUDA-event time of the iteration kernels (if profiling) */
+  double total_ms;         /* CUDA-event time of the whole call (if profiling)        */
+} ss_run_stats;
+
+/*
+ * Build the SlimSell layout from a CSR graph on the device (Sections II-D, III-B).
+ *   d_row_ptr  int64[n + 1], d_col int32[nnz]: symmetric graph without
+ *              self-loops or duplicate entries (not checked); neighbour lists
+ *              sorted by ascending id.  Not retained after the call returns.
+ *   C          chunk height, one of 8, 16, 32, 64.
+ *   sigma      sorting scope: rows are sorted by descending degree (ties by
+ *              ascending id) inside windows of sigma consecutive vertices;
+ *              sigma <= 1 keeps the input order, sigma >= n sorts globally.
+ *   split_w    SlimChunk width: chunks with more than split_w columns are split
+ *              into ceil(cl / split_w) work items (Section III-D); 0 disables.
+ * The call synchronises `stream` (it needs the layout size to allocate col).
+ * Errors: SS_ERR_INVALID (n < 1, nnz < 0, bad C, sigma < 1, split_w < 0,
+ * NULL pointers), SS_ERR_OOM, SS_ERR_CUDA.  *out is NULL on failure.
+ */
+ss_status slimsell_build(const int64_t* d_row_ptr, const int32_t* d_col, int32_t n, int64_t nnz,
+                         int32_t C, int32_t sigma, int32_t split_w, void* stream,
+                         slimsell_handle* out);
+
+/*
+ * Single-source BFS (Section III-A semiring BFS-SpMV; SlimWork Section III-C;
+ * SlimChunk Section III-D; DP Section II-C for non-sel-max parents).
+ *   root       vertex id in [0, n).
+ *   semiring   ss_semiring.
+ *   policy     ss_policy.
+ *   d_dist     int32[n] or NULL; d_parent int32[n] or NULL (NULL skips the DP pass).
+ * Returns after the BFS has finished on `stream` (the iteration loop reads one
+ * counter per iteration).  Errors: SS_ERR_INVALID, SS_ERR_CUDA, SS_ERR_UNSUPPORTED.
+ */
+ss_status slimsell_bfs(slimsell_handle h, int32_t root, int32_t semiring, int32_t policy,
+                       int32_t* d_dist, int32_t* d_parent, void* stream);
+
+/* Layout summary. */
+ss_status slimsell_get_info(slimsell_handle h, ss_info* out);
+
+/*
+ * Statistics of the last slimsell_bfs on this handle.  h_iters (host, may be
+ * NULL) receives up to cap per-iteration records.
+ */
+ss_status slimsell_get_run_stats(slimsell_handle h, ss_run_stats* out, ss_iter_stats* h_iters,
+                                 int32_t cap);
+
+/* Record CUDA events around the iteration kernels of later calls (0 = off). */
+ss_status slimsell_set_profiling(slimsell_handle h, int32_t on);
+
+/*
+ * Copy the layout into caller-owned device buffers (any may be NULL):
+ *   d_perm int32[n_chunks * C] (vertex at each row position, -1 for padding rows),
+ *   d_cl int32[n_chunks], d_cs int64[n_chunks + 1], d_col int32[slots],
+ *   d_items int32[4 * n_items] as (chunk, j0, j1, split index or -1).
+ * Synchronises `stream`.
+ */
+ss_status slimsell_export_layout(slimsell_handle h, int32_t* d_perm, int32_t* d_cl, int64_t* d_cs,
+                                 int32_t* d_col, int32_t* d_items, void* stream);
+
+/* Free the handle and its device buffers (NULL is ignored). */
+void slimsell_destroy(slimsell_handle h);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* slimsell_last_error(void);
+
+/* Library version string. */
+const char* slimsell_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SLIMSELL_H */

@@ -1,0 +1,225 @@
+"""Python binding of libslimsell (GB300 SlimSell BFS), marshalling only.
+
+Every function here is a thin ctypes wrapper of the C entry point with the same
+name in ``include/slimsell.h``; all computation runs in the library's CUDA
+kernels.  PyTorch supplies device memory (tensors) and streams.  There is no
+CPU fallback: if ``libslimsell.so`` is missing or cannot be loaded, every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from .build import LIB, build  # noqa: F401  (build() compiles the library)
+
+TROPICAL, REAL, BOOLEAN, SELMAX = 0, 1, 2, 3
+SEMIRINGS = {"tropical": TROPICAL, "real": REAL, "boolean": BOOLEAN, "selmax": SELMAX}
+V_FULL, V_SLIMWORK, V_PUSH, V_PULL_FILTERED, V_HEURISTIC, V_LEARNED = range(6)
+POLICIES = {"full": V_FULL, "slimwork": V_SLIMWORK, "push": V_PUSH,
+            "pull_filtered": V_PULL_FILTERED, "heuristic": V_HEURISTIC, "learned": V_LEARNED}
+STATUS = {0: "SS_OK", 1: "SS_ERR_INVALID", 2: "SS_ERR_OOM", 3: "SS_ERR_CUDA",
+          4: "SS_ERR_TIMEOUT", 5: "SS_ERR_UNSUPPORTED"}
+
+
+class SlimSellError(RuntimeError):
+    def __init__(self, fn: str, status: int, msg: str):
+        super().__init__(f"{fn}: {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class ss_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("C", ctypes.c_int32), ("sigma", ctypes.c_int32),
+                ("split_w", ctypes.c_int32), ("n_chunks", ctypes.c_int32),
+                ("n_items", ctypes.c_int32), ("n_split_chunks", ctypes.c_int32),
+                ("max_degree", ctypes.c_int32), ("nnz", ctypes.c_int64), ("slots", ctypes.c_int64),
+                ("padding", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+
+
+class ss_iter_stats(ctypes.Structure):
+    _fields_ = [("frontier", ctypes.c_int64), ("frontier_degree", ctypes.c_int64),
+                ("slots", ctypes.c_int64), ("active_chunks", ctypes.c_int64),
+                ("variant", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class ss_run_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("semiring", ctypes.c_int32),
+                ("reached", ctypes.c_int64), ("reached_degree", ctypes.c_int64),
+                ("slots", ctypes.c_int64), ("dp_slots", ctypes.c_int64),
+                ("iter_kernel_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
+
+
+_lib = None
+_VP = ctypes.c_void_p
+
+
+def lib():
+    """Load libslimsell.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB):
+        raise RuntimeError(f"{LIB} is missing; run paper_2010_09913_gb300.build.build() first")
+    L = ctypes.CDLL(LIB)
+    i32, i64 = ctypes.c_int32, ctypes.c_int64
+    sigs = {
+        "slimsell_build": (i32, [_VP, _VP, i32, i64, i32, i32, i32, _VP, ctypes.POINTER(_VP)]),
+        "slimsell_bfs": (i32, [_VP, i32, i32, i32, _VP, _VP, _VP]),
+        "slimsell_get_info": (i32, [_VP, ctypes.POINTER(ss_info)]),
+        "slimsell_get_run_stats": (i32, [_VP, ctypes.POINTER(ss_run_stats),
+                                         ctypes.POINTER(ss_iter_stats), i32]),
+        "slimsell_set_profiling": (i32, [_VP, i32]),
+        "slimsell_export_layout": (i32, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+        "slimsell_destroy": (None, [_VP]),
+        "slimsell_last_error": (ctypes.c_char_p, []),
+        "slimsell_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def exported_symbols() -> list[str]:
+    return ["slimsell_build", "slimsell_bfs", "slimsell_get_info", "slimsell_get_run_stats",
+            "slimsell_set_profiling", "slimsell_export_layout", "slimsell_destroy",
+            "slimsell_last_error", "slimsell_version"]
+
+
+def _check(fn: str, status: int):
+    if status != 0:
+        raise SlimSellError(fn, status, lib().slimsell_last_error().decode())
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr(t: torch.Tensor | None, dtype: torch.dtype, name: str):
+    if t is None:
+        return None
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA tensor of {dtype}")
+    return t.data_ptr()
+
+
+# ---- C entry points, same names -------------------------------------------------------
+
+def slimsell_build(row_ptr: torch.Tensor, col: torch.Tensor, n: int, nnz: int, C: int, sigma: int,
+                   split_w: int, stream=None) -> int:
+    h = _VP()
+    _check("slimsell_build", lib().slimsell_build(
+        _ptr(row_ptr, torch.int64, "row_ptr"), _ptr(col, torch.int32, "col"), int(n), int(nnz),
+        int(C), int(sigma), int(split_w), _stream(stream), ctypes.byref(h)))
+    return h.value
+
+
+def slimsell_bfs(h: int, root: int, semiring: int, policy: int, dist: torch.Tensor | None,
+                 parent: torch.Tensor | None, stream=None) -> None:
+    _check("slimsell_bfs", lib().slimsell_bfs(
+        h, int(root), int(semiring), int(policy), _ptr(dist, torch.int32, "dist"),
+        _ptr(parent, torch.int32, "parent"), _stream(stream)))
+
+
+def slimsell_get_info(h: int) -> ss_info:
+    out = ss_info()
+    _check("slimsell_get_info", lib().slimsell_get_info(h, ctypes.byref(out)))
+    return out
+
+
+def slimsell_get_run_stats(h: int, cap: int = 0):
+    out = ss_run_stats()
+    arr = (ss_iter_stats * cap)() if cap > 0 else None
+    _check("slimsell_get_run_stats", lib().slimsell_get_run_stats(h, ctypes.byref(out), arr, int(cap)))
+    return out, arr
+
+
+def slimsell_set_profiling(h: int, on: bool) -> None:
+    _check("slimsell_set_profiling", lib().slimsell_set_profiling(h, 1 if on else 0))
+
+
+def slimsell_export_layout(h: int, perm, cl, cs, col, items, stream=None) -> None:
+    _check("slimsell_export_layout", lib().slimsell_export_layout(
+        h, _ptr(perm, torch.int32, "perm"), _ptr(cl, torch.int32, "cl"), _ptr(cs, torch.int64, "cs"),
+        _ptr(col, torch.int32, "col"), _ptr(items, torch.int32, "items"), _stream(stream)))
+
+
+def slimsell_destroy(h: int) -> None:
+    if h:
+        lib().slimsell_destroy(h)
+
+
+def slimsell_last_error() -> str:
+    return lib().slimsell_last_error().decode()
+
+
+def slimsell_version() -> str:
+    return lib().slimsell_version().decode()
+
+
+# ---- convenience wrapper ---------------------------------------------------------------
+
+class SlimSellGraph:
+    """Owns one built handle; tensors stay on the caller's device."""
+
+    def __init__(self, row_ptr: torch.Tensor, col: torch.Tensor, C: int = 32, sigma: int | None = None,
+                 split_w: int = 1024, stream=None):
+        n = row_ptr.numel() - 1
+        self.n = n
+        self.h = slimsell_build(row_ptr, col, n, col.numel(), C, n if sigma is None else sigma,
+                                split_w, stream)
+
+    @classmethod
+    def from_host(cls, row_ptr, col, device="cuda", **kw):
+        rp = torch.as_tensor(row_ptr, dtype=torch.int64).to(device)
+        c = torch.as_tensor(col, dtype=torch.int32).to(device)
+        if c.numel() == 0:
+            c = torch.zeros(1, dtype=torch.int32, device=device)[:0]
+        return cls(rp, c, **kw)
+
+    def info(self) -> ss_info:
+        return slimsell_get_info(self.h)
+
+    def bfs(self, root: int, semiring="tropical", policy="slimwork", dist=None, parent=None,
+            want_parent: bool = True, stream=None):
+        sr = SEMIRINGS[semiring] if isinstance(semiring, str) else int(semiring)
+        pol = POLICIES[policy] if isinstance(policy, str) else int(policy)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if dist is None:
+            dist = torch.empty(self.n, dtype=torch.int32, device=dev)
+        if parent is None and want_parent:
+            parent = torch.empty(self.n, dtype=torch.int32, device=dev)
+        slimsell_bfs(self.h, root, sr, pol, dist, parent, stream)
+        return dist, parent
+
+    def run_stats(self, cap: int = 0):
+        return slimsell_get_run_stats(self.h, cap)
+
+    def export_layout(self):
+        inf = self.info()
+        dev = torch.device("cuda", torch.cuda.current_device())
+        perm = torch.empty(inf.n_chunks * inf.C, dtype=torch.int32, device=dev)
+        cl = torch.empty(inf.n_chunks, dtype=torch.int32, device=dev)
+        cs = torch.empty(inf.n_chunks + 1, dtype=torch.int64, device=dev)
+        col = torch.empty(max(inf.slots, 1), dtype=torch.int32, device=dev)
+        items = torch.empty(max(inf.n_items, 1) * 4, dtype=torch.int32, device=dev)
+        slimsell_export_layout(self.h, perm, cl, cs, col, items)
+        return {"perm": perm, "cl": cl, "cs": cs, "col": col[: inf.slots],
+                "items": items[: inf.n_items * 4].view(-1, 4)}
+
+    def close(self):
+        if getattr(self, "h", None):
+            slimsell_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

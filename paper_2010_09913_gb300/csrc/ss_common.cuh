@@ -1,0 +1,108 @@
+// Internal definitions shared by the CUDA translation units of libslimsell.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <string>
+
+#include "slimsell.h"
+
+#define SS_INF 0x7fffffff          // tropical infinity / "unvisited" level
+#define SS_PAD_LEVEL (-1)          // level of padding rows (never unvisited, never in a frontier)
+#define SS_FULL_MASK 0xffffffffu
+
+namespace ss {
+
+void set_error(const char* fmt, ...);
+ss_status cuda_fail(cudaError_t e, const char* what);
+
+#define SS_CUDA(call)                                                   \
+  do {                                                                  \
+    cudaError_t _e = (call);                                            \
+    if (_e != cudaSuccess) return ::ss::cuda_fail(_e, #call);           \
+  } while (0)
+
+// Device control block for one BFS run (one per handle).
+struct Ctl {
+  int k;          // level being discovered by the current iteration
+  int done;       // 1 once an iteration discovered nothing
+  int error;      // device-side error flags
+  int variant;    // variant executed by the current iteration
+  unsigned long long new_count;   // vertices discovered by the current iteration
+  unsigned long long new_deg;     // their degree sum
+  unsigned long long slots;       // col slots read by the current iteration
+  unsigned long long active;      // chunks processed by the current iteration
+  unsigned long long reached;     // cumulative vertices reached
+  unsigned long long reached_deg; // cumulative degree sum
+  unsigned long long total_slots; // cumulative slots
+  unsigned long long dp_slots;    // slots read by the DP pass
+};
+
+// Flat view of the handle's device buffers handed to kernels by value.
+struct Dev {
+  int n, C, n_c, n_pad, n_items, n_split;
+  const int* perm;      // [n_pad] vertex at row position (-1 for padding rows)
+  const int* invperm;   // [n] row position of vertex
+  const int* rdeg;      // [n_pad] degree of the vertex at each row (0 for padding)
+  const int* cl;        // [n_c] chunk lengths
+  const long long* cs;  // [n_c + 1] chunk starts (in slots)
+  const int* col;       // [slots] SlimSell column array (-1 = padding)
+  const int4* items;    // [n_items] (chunk, j0, j1, split index or -1)
+  const int* split_n;   // [n_split] items per split chunk
+  int* lvl;             // [n_pad] level (SS_INF = unvisited); the tropical f vector
+  unsigned char* act;   // [n_c] SlimWork state: 1 active, 3/2 inactive with zero writes pending, 0 inactive
+  unsigned* fb[2];      // boolean frontier bitmaps (n_pad bits each), indexed by level parity
+  float* fr[2];         // real-semiring frontier values, by level parity
+  int* fx[2];           // sel-max frontier ids (original id + 1, 0 = not in frontier), by parity
+  int* par;             // [n_pad] parents: sel-max p vector (id + 1) / DP result (original id)
+  unsigned* xacc;       // [n_split * C] SlimChunk partial results (semiring-typed bits)
+  unsigned* arrive;     // [n_split] SlimChunk arrival counters
+  Ctl* ctl;
+  ss_iter_stats* iters; // [iter_cap]
+  int iter_cap;
+};
+
+}  // namespace ss
+
+struct slimsell_graph {
+  int device = 0;
+  int n = 0, C = 0, sigma = 0, split_w = 0, n_c = 0, n_pad = 0;
+  long long nnz = 0, slots = 0;
+  int n_items = 0, n_split = 0, max_degree = 0;
+  int num_sms = 0;
+  // layout
+  int* perm = nullptr;
+  int* invperm = nullptr;
+  int* rdeg = nullptr;
+  int* cl = nullptr;
+  long long* cs = nullptr;
+  int* col = nullptr;
+  int4* items = nullptr;
+  int* split_n = nullptr;
+  // BFS state
+  int* lvl = nullptr;
+  unsigned char* act = nullptr;
+  unsigned* fb[2] = {nullptr, nullptr};
+  float* fr[2] = {nullptr, nullptr};
+  int* fx[2] = {nullptr, nullptr};
+  int* par = nullptr;
+  unsigned* xacc = nullptr;
+  unsigned* arrive = nullptr;
+  ss::Ctl* ctl = nullptr;
+  ss::Ctl* h_ctl = nullptr;  // pinned host copy
+  ss_iter_stats* iters = nullptr;
+  int iter_cap = 0;
+  long long device_bytes = 0;
+  // last run
+  ss_run_stats last{};
+  int profiling = 0;
+  cudaEvent_t ev_a = nullptr, ev_b = nullptr, ev_c = nullptr, ev_d = nullptr;
+
+  ss::Dev dev() const;
+};
+
+namespace ss {
+ss_status dmalloc(slimsell_graph* h, void** p, size_t bytes);
+}  // namespace ss

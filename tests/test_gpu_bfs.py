@@ -1,0 +1,189 @@
+"""GPU parity: SlimSell BFS through the C ABI vs the CPU oracle, bit-exact.
+
+Distances and parents are integers and must match exactly (parents are the
+canonical max-id parent for every semiring).  Iteration counts and the number
+of vertices discovered per iteration must match the oracle's semiring BFS.
+"""
+import numpy as np
+import pytest
+import torch
+
+import graphgen as gg
+import oracle
+import paper_2010_09913_gb300 as ss
+
+pytestmark = pytest.mark.gpu
+
+SEMIRINGS = ["tropical", "real", "boolean", "selmax"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _build():
+    ss.build()
+    assert torch.cuda.is_available()
+
+
+def expected(g, r):
+    d = oracle.bfs_queue(g.row_ptr, g.col, int(r))
+    return d, oracle.dp(g.row_ptr, g.col, d, int(r))
+
+
+def run(G, r, sr, pol):
+    dist, parent = G.bfs(int(r), sr, pol)
+    torch.cuda.synchronize()
+    return dist.cpu().numpy(), parent.cpu().numpy()
+
+
+def check_stats(G, g, r, sr):
+    _, _, _, it, levels = oracle.bfs_semiring(g.row_ptr, g.col, int(r), sr)
+    st, iters = G.run_stats(cap=it + 1)
+    assert st.iterations == it
+    got = np.array([iters[i].frontier for i in range(it + 1)])
+    np.testing.assert_array_equal(got[: len(levels)], levels)
+    d = oracle.bfs_queue(g.row_ptr, g.col, int(r))
+    assert st.reached == int((d >= 0).sum())
+    assert st.reached_degree == 2 * oracle.reached_edges(g.row_ptr, d)
+
+
+@pytest.mark.parametrize("sr", SEMIRINGS)
+@pytest.mark.parametrize("pol", ["full", "slimwork"])
+def test_kron14_parity(sr, pol):
+    """Kronecker scale 14, C = 32, sigma = n (the small configuration), several roots."""
+    g = gg.kronecker(14, seed=1)
+    G = ss.SlimSellGraph.from_host(g.row_ptr, g.col, C=32, sigma=g.n, split_w=256)
+    for r in gg.roots(g, 4, seed=2):
+        d, p = expected(g, r)
+        dist, parent = run(G, r, sr, pol)
+        np.testing.assert_array_equal(dist, d)
+        np.testing.assert_array_equal(parent, p)
+        check_stats(G, g, r, sr)
+    G.close()
+
+
+@pytest.mark.parametrize("C", [8, 16, 32, 64])
+@pytest.mark.parametrize("sigma_kind", ["one", "window", "full"])
+@pytest.mark.parametrize("split_w", [0, 16])
+def test_layout_independence(C, sigma_kind, split_w):
+    g = gg.kronecker(11, seed=3)
+    sigma = {"one": 1, "window": 256, "full": g.n}[sigma_kind]
+    G = ss.SlimSellGraph.from_host(g.row_ptr, g.col, C=C, sigma=sigma, split_w=split_w)
+    r = int(gg.roots(g, 1, seed=5)[0])
+    d, p = expected(g, r)
+    for sr in SEMIRINGS:
+        dist, parent = run(G, r, sr, "slimwork")
+        np.testing.assert_array_equal(dist, d, err_msg=sr)
+        np.testing.assert_array_equal(parent, p, err_msg=sr)
+    G.close()
+
+
+@pytest.mark.parametrize("C", [8, 32, 64])
+def test_layout_matches_oracle(C):
+    for g in [gg.kronecker(10, seed=4), gg.lattice(23, 0.1, seed=2)]:  # n = 529 is ragged
+        for sigma in (1, 64, g.n):
+            for split_w in (0, 7):
+                G = ss.SlimSellGraph.from_host(g.row_ptr, g.col, C=C, sigma=sigma, split_w=split_w)
+                L = oracle.slimsell_layout(g.row_ptr, g.col, C, sigma, split_w)
+                got = {k: v.cpu().numpy() for k, v in G.export_layout().items()}
+                perm = L["perm"]
+                np.testing.assert_array_equal(got["perm"][: g.n], perm)
+                assert np.all(got["perm"][g.n:] == -1)
+                np.testing.assert_array_equal(got["cl"], L["cl"])
+                np.testing.assert_array_equal(got["cs"], L["cs"])
+                np.testing.assert_array_equal(got["col"], L["col"])
+                np.testing.assert_array_equal(got["items"][:, :3], L["items"])
+                inf = G.info()
+                assert inf.slots == L["cs"][-1] and inf.padding == L["padding"]
+                assert inf.max_degree == int(g.degrees().max())
+                G.close()
+
+
+def test_edge_cases():
+    cases = [
+        gg.from_edges(1, []),                                      # single vertex, no edges
+        gg.from_edges(5, [(0, 1)]),                                # isolated vertices
+        gg.from_edges(70, [(i, i + 1) for i in range(69)]),        # long path, ragged n
+        gg.from_edges(40, [(0, i) for i in range(1, 40)]),         # star: hub chunk split
+        gg.from_edges(33, [(i, j) for i in range(33) for j in range(i + 1, 33)]),  # complete
+        gg.from_edges(9, [(0, 1), (1, 2), (5, 6), (6, 7), (7, 5)]),  # disconnected
+        gg.lattice(17, 0.0, seed=1),
+    ]
+    for g in cases:
+        for C, split_w in [(8, 0), (32, 4), (64, 2)]:
+            G = ss.SlimSellGraph.from_host(g.row_ptr, g.col, C=C, sigma=g.n, split_w=split_w)
+            for r in sorted({0, g.n - 1, g.n // 2}):
+                d, p = expected(g, r)
+                for sr in SEMIRINGS:
+                    for pol in ("full", "slimwork"):
+                        dist, parent = run(G, r, sr, pol)
+                        np.testing.assert_array_equal(dist, d, err_msg=f"{g.name} {sr} {pol} r={r}")
+                        np.testing.assert_array_equal(parent, p, err_msg=f"{g.name} {sr} {pol}")
+            G.close()
+
+
+def test_lattice_and_er_parity():
+    for g in [gg.lattice(64, 0.05, seed=1), gg.erdos_renyi(1 << 14, 16.0, seed=1)]:
+        G = ss.SlimSellGraph.from_host(g.row_ptr, g.col, C=32, sigma=g.n, split_w=1024)
+        for r in gg.roots(g, 2, seed=2):
+            d, p = expected(g, r)
+            for sr in ("selmax", "tropical"):
+                dist, parent = run(G, r, sr, "slimwork")
+                np.testing.assert_array_equal(dist, d)
+                np.testing.assert_array_equal(parent, p)
+                check_stats(G, g, r, sr)
+        G.close()
+
+
+def test_outputs_optional():
+    g = gg.kronecker(9, seed=2)
+    G = ss.SlimSellGraph.from_host(g.row_ptr, g.col)
+    r = int(gg.roots(g, 1, seed=1)[0])
+    d, _ = expected(g, r)
+    dist = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    ss.slimsell_bfs(G.h, r, ss.TROPICAL, ss.V_SLIMWORK, dist, None)
+    np.testing.assert_array_equal(dist.cpu().numpy(), d)
+    ss.slimsell_bfs(G.h, r, ss.BOOLEAN, ss.V_SLIMWORK, None, None)  # nothing written, still runs
+    G.close()
+
+
+def test_invalid_arguments_on_gpu():
+    g = gg.kronecker(8, seed=2)
+    G = ss.SlimSellGraph.from_host(g.row_ptr, g.col)
+    dist = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    with pytest.raises(ss.SlimSellError) as e:
+        ss.slimsell_bfs(G.h, g.n, 0, 1, dist, None)
+    assert e.value.status == 1
+    with pytest.raises(ss.SlimSellError):
+        ss.slimsell_bfs(G.h, 0, 7, 1, dist, None)
+    with pytest.raises(ss.SlimSellError):
+        ss.slimsell_bfs(G.h, 0, 0, 99, dist, None)
+    G.close()
+
+
+@pytest.mark.parametrize("sr", SEMIRINGS)
+def test_kron22_sampled_parity(sr):
+    """Full-size Kronecker scale 22 (the main benchmark graph), 2 roots, SlimWork + SlimChunk."""
+    g = _kron22()
+    G = _kron22_handle()
+    for r in gg.roots(g, 2, seed=2):
+        d, p = expected(g, r)
+        dist, parent = run(G, r, sr, "slimwork")
+        np.testing.assert_array_equal(dist, d)
+        np.testing.assert_array_equal(parent, p)
+        st, _ = G.run_stats()
+        assert st.reached_degree == 2 * oracle.reached_edges(g.row_ptr, d)
+
+
+_cache = {}
+
+
+def _kron22():
+    if "g" not in _cache:
+        _cache["g"] = gg.kronecker(22, seed=1)
+    return _cache["g"]
+
+
+def _kron22_handle():
+    if "G" not in _cache:
+        g = _kron22()
+        _cache["G"] = ss.SlimSellGraph.from_host(g.row_ptr, g.col, C=32, sigma=g.n, split_w=1024)
+    return _cache["G"]
