@@ -1,0 +1,458 @@
+"""Benchmark: SlimSell BFS-SpMV on one GB300 (GTEPS and fraction of HBM roofline).
+
+Workload (default): undirected Kronecker graph, scale 22, edgefactor 16,
+initiator (0.57, 0.19, 0.19, 0.05), cleaned and label-permuted (seed 1); 64
+seeded roots run one at a time for each of the four semirings (tropical, real
+with fp32 values, boolean, sel-max); C = 32, sigma = n, SlimWork on, SlimChunk
+width 1024; every run produces int32 distances and parents (DP for the
+non-sel-max semirings).  A step is all 256 runs.
+
+Prints ONE JSON line.  `--impl reference` times the CPU oracle (the plain CSR
+semiring BFS) on the host cores instead, on a bounded sample of the same
+workload.  Under torchrun every rank runs its own 64 roots (weak scaling, no
+data-path collective; the graph is replicated).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import graphgen as gg  # noqa: E402
+
+METRIC = "GTEPS and % of HBM roofline per semiring, batched+learned vs plain single-source"
+SEMIRINGS = ["tropical", "real", "boolean", "selmax"]
+SR_ID = {"tropical": 0, "real": 1, "boolean": 2, "selmax": 3}
+# bytes per vertex of the gathered frontier vector and of the per-row frontier write
+FRONTIER_BYTES = {"tropical": 4.0, "real": 4.0, "boolean": 0.125, "selmax": 4.0}
+FRONTIER_WRITE = {"tropical": 0.0, "real": 4.0, "boolean": 0.125, "selmax": 4.0}
+
+# DRAM traffic per k_pull launch measured by ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum) on this workload, keyed by the hash of the kernel source
+# it was taken on; reported as null once the source changes.
+NCU_TRAFFIC = {}
+
+
+def kernel_source_hash() -> str:
+    p = os.path.join(ROOT, "paper_2010_09913_gb300", "csrc", "ss_bfs.cu")
+    with open(p, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def iteration_bytes(it, sr: str, n: int, C: int) -> float:
+    """Algorithmic bytes of one pull iteration (SlimSell slots, chunk tables,
+    own-row state, discoveries, one pass over the gathered frontier vector)."""
+    rows = C * it.active_chunks
+    b = 4.0 * it.slots                      # col slots of processed chunks (incl. padding)
+    b += 8.0 * it.active_chunks             # cs / cl
+    b += rows * (4.0 + FRONTIER_WRITE[sr])  # own-row level read + frontier write
+    b += it.frontier * (4.0 + 4.0)          # level write + degree read of new vertices
+    if sr == "selmax":
+        b += it.frontier * 4.0              # parent write
+    b += n * FRONTIER_BYTES[sr]             # gathered frontier vector, once (L2-served)
+    return b
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    def __init__(self, index: int):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if os.environ.get("SS_BENCH_GLOO") is None else "gloo"
+        dist.init_process_group(backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, x: float, device=None) -> float:
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(pg, x: float, device=None) -> float:
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return float(t.item())
+
+
+def cpu_oracle_sample(g, roots, budget_s: float):
+    """Time the oracle's plain CSR semiring BFS (all four semirings, DP parents)
+    on one core, root after root, until the budget is used."""
+    import oracle
+    oracle.build()
+    edges, t_total, runs = 0, 0.0, 0
+    for r in roots:
+        for sr in SEMIRINGS:
+            t0 = time.perf_counter()
+            dist, parent, _, _, _ = oracle.bfs_semiring(g.row_ptr, g.col, int(r), sr)
+            t_total += time.perf_counter() - t0
+            edges += oracle.reached_edges(g.row_ptr, dist)
+            runs += 1
+        if t_total >= budget_s:
+            break
+    return edges, t_total, runs
+
+
+def run_reference(args, world, rank, pg):
+    if rank != 0:
+        return
+    g = gg.kronecker(args.scale, seed=1)
+    roots = gg.roots(g, args.roots, seed=2)
+    per_step = max(10.0, min(30.0, 150.0 / max(1, args.steps + args.warmup)))
+    import oracle
+    oracle.build()
+    idx = 0
+    times, edges_l = [], []
+    for s in range(args.warmup + args.steps):
+        edges, t_tot, runs = 0, 0.0, 0
+        while t_tot < per_step or runs == 0:
+            r = int(roots[idx % len(roots)])
+            idx += 1
+            for sr in SEMIRINGS:
+                t0 = time.perf_counter()
+                dist, _, _, _, _ = oracle.bfs_semiring(g.row_ptr, g.col, r, sr)
+                t_tot += time.perf_counter() - t0
+                edges += oracle.reached_edges(g.row_ptr, dist)
+                runs += 1
+        if s >= args.warmup:
+            times.append(t_tot)
+            edges_l.append(edges)
+    value = sum(edges_l) / sum(times) / 1e9
+    ms = 1000.0 * sum(times) / len(times)
+    sample = (f"oracle semiring BFS (plain CSR, fp64, serial C), all 4 semirings per root, "
+              f"~{per_step:.0f} s of roots per step on kronecker scale {args.scale}")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GTEPS",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": workload_config(args, g),
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample, "value": value,
+                             "unit": "GTEPS"},
+            "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args, g):
+    return {"workload": f"kronecker scale {args.scale} edgefactor 16, {args.roots} roots one at a "
+                        f"time x 4 semirings, C=32, sigma=n, SlimWork + SlimChunk w={args.split_w}",
+            "graph": {"n": g.n, "nnz": g.nnz, "undirected_edges": g.m},
+            "semirings": SEMIRINGS, "C": 32, "sigma": "n", "split_w": args.split_w,
+            "l2": f"inputs larger than L2: SlimSell col is ~{(g.nnz * 4) >> 20} MiB+ (L2 129 MB)",
+            "outputs": "int32 dist + parent per run (DP for tropical/real/boolean)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=int, default=22)
+    ap.add_argument("--roots", type=int, default=64)
+    ap.add_argument("--split-w", type=int, default=1024)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-ablations", action="store_true")
+    args = ap.parse_args()
+    world, rank, local, pg = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank, pg)
+        return
+
+    import torch
+    import paper_2010_09913_gb300 as ss
+    ss.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+
+    g = gg.kronecker(args.scale, seed=1)
+    roots = gg.roots(g, args.roots, seed=2 + 1000 * rank)
+    n = g.n
+    rp_d = torch.from_numpy(g.row_ptr).to(dev)
+    col_d = torch.from_numpy(g.col).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h = ss.slimsell_build(rp_d, col_d, n, g.nnz, 32, n, args.split_w, stream)
+    torch.cuda.synchronize()
+    build_ms = 1000.0 * (time.perf_counter() - t0)
+    info = ss.slimsell_get_info(h)
+    dist = torch.empty(n, dtype=torch.int32, device=dev)
+    parent = torch.empty(n, dtype=torch.int32, device=dev)
+
+    # one untimed pass collects the deterministic per-run statistics
+    ss.slimsell_set_profiling(h, True)
+    runs = []
+    for sr in SEMIRINGS:
+        for r in roots:
+            ss.slimsell_bfs(h, int(r), SR_ID[sr], ss.V_SLIMWORK, dist, parent, stream)
+            st, iters = ss.slimsell_get_run_stats(h, cap=4096)
+            its = [iters[i] for i in range(1, min(st.iterations, 4095) + 1)]
+            pull_bytes = sum(iteration_bytes(it, sr, n, 32) for it in its)
+            launches = 2 + 2 * st.iterations + (1 if sr != "selmax" else 0) + 1
+            runs.append({"sr": sr, "root": int(r), "edges": st.reached_degree // 2,
+                         "iterations": st.iterations, "pull_bytes": pull_bytes,
+                         "slots": st.slots, "dp_slots": st.dp_slots, "launches": launches})
+    edges_per_step = sum(x["edges"] for x in runs)
+    launches_per_step = sum(x["launches"] for x in runs)
+    pull_bytes_per_step = sum(x["pull_bytes"] for x in runs)
+    pull_launches_per_step = sum(x["iterations"] for x in runs)
+
+    def step(record=None):
+        for sr in SEMIRINGS:
+            if record is not None:
+                record[sr][0].record(stream)
+            for r in roots:
+                ss.slimsell_bfs(h, int(r), SR_ID[sr], ss.V_SLIMWORK, dist, parent, stream)
+                if record is not None:
+                    record["pull_ms"] += ss.slimsell_get_run_stats(h)[0].iter_kernel_ms
+            if record is not None:
+                record[sr][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(pg)
+    clocks = Clocks(local)
+    rec = {sr: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for sr in SEMIRINGS}
+    rec["pull_ms"] = 0.0
+    per_sr_ms = {sr: 0.0 for sr in SEMIRINGS}
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step(rec)
+        torch.cuda.synchronize()
+        for sr in SEMIRINGS:
+            per_sr_ms[sr] += rec[sr][0].elapsed_time(rec[sr][1])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    total_ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    barrier(pg)
+    total_ms_max = max_over_ranks(pg, total_ms, dev)
+    edges_all = sum_over_ranks(pg, float(edges_per_step * args.steps), dev)
+    value = edges_all / (total_ms_max / 1000.0) / 1e9
+    hbm, peak_kind = load_peaks()
+    pull_ms = rec["pull_ms"]
+    achieved = pull_bytes_per_step * args.steps / (pull_ms / 1000.0) / 1e9 if pull_ms > 0 else 0.0
+    per_sr = {}
+    for sr in SEMIRINGS:
+        e = sum(x["edges"] for x in runs if x["sr"] == sr) * args.steps
+        b = sum(x["pull_bytes"] for x in runs if x["sr"] == sr) * args.steps
+        ms = per_sr_ms[sr]
+        per_sr[sr] = {"gteps": e / (ms / 1000.0) / 1e9,
+                      "ms_per_run": ms / (args.steps * len(roots)),
+                      "pull_bytes_per_run": b / (args.steps * len(roots)),
+                      "whole_run_gbs": b / (ms / 1000.0) / 1e9,
+                      "whole_run_hbm_frac": b / (ms / 1000.0) / 1e9 / hbm}
+    traffic = NCU_TRAFFIC.get(kernel_source_hash())
+
+    line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": workload_config(args, g),
+            "gpu_launches": launches_per_step * args.steps,
+            "roofline": {"bound": "hbm", "kernel": "k_pull (SlimSell pull iteration)",
+                         "achieved": achieved, "peak": hbm, "peak_kind": peak_kind,
+                         "unit": "GB/s", "frac": achieved / hbm,
+                         "traffic": traffic,
+                         "algorithmic_bytes_per_launch": pull_bytes_per_step / max(1, pull_launches_per_step),
+                         "avg_launch_ms": pull_ms / max(1, pull_launches_per_step * args.steps),
+                         "frac_of_nominal_8tbs": achieved / 8000.0},
+            "per_semiring": per_sr, "clocks": clk,
+            "build_ms": build_ms,
+            "layout": {"slots": info.slots, "padding": info.padding, "n_items": info.n_items,
+                       "n_split_chunks": info.n_split_chunks, "max_degree": info.max_degree}}
+
+    ss.slimsell_set_profiling(h, False)
+    if not args.no_e2e:
+        line["e2e"] = e2e_measure(ss, torch, g, roots, args, stream, dev, pg)
+    if not args.no_ablations and rank == 0:
+        line["ablations"] = ablations(ss, torch, g, roots[:8], h, rp_d, col_d, args, stream, dev)
+    ss.slimsell_destroy(h)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        edges, t_cpu, nruns = cpu_oracle_sample(g, roots, 20.0)
+        line["cpu_baseline"] = {"value": edges / t_cpu / 1e9, "unit": "GTEPS", "cores": 1,
+                                "kind": "oracle",
+                                "sample": f"{nruns} runs (roots x 4 semirings) of the oracle's plain "
+                                          f"CSR semiring BFS on kronecker scale {args.scale}, serial"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+def e2e_measure(ss, torch, g, roots, args, stream, dev, pg):
+    """Same metric through the public C ABI from host memory: per step, pinned
+    host CSR -> device, build, every run, device -> pinned host dist + parent."""
+    n = g.n
+    rp_h = torch.from_numpy(g.row_ptr).pin_memory()
+    col_h = torch.from_numpy(g.col).pin_memory()
+    out_h = torch.empty((2, n), dtype=torch.int32).pin_memory()
+    dist = torch.empty(n, dtype=torch.int32, device=dev)
+    parent = torch.empty(n, dtype=torch.int32, device=dev)
+    edges = 0
+    h2d = rp_h.numel() * 8 + col_h.numel() * 4
+    d2h = 0
+
+    def one_step():
+        nonlocal edges, d2h
+        rp_d = rp_h.to(dev, non_blocking=True)
+        col_d = col_h.to(dev, non_blocking=True)
+        h = ss.slimsell_build(rp_d, col_d, n, g.nnz, 32, n, args.split_w, stream)
+        e, b = 0, 0
+        for sr in SEMIRINGS:
+            for r in roots:
+                ss.slimsell_bfs(h, int(r), SR_ID[sr], ss.V_SLIMWORK, dist, parent, stream)
+                out_h[0].copy_(dist, non_blocking=True)
+                out_h[1].copy_(parent, non_blocking=True)
+                e += ss.slimsell_get_run_stats(h)[0].reached_degree // 2
+                b += 8 * n
+        torch.cuda.current_stream().synchronize()
+        ss.slimsell_destroy(h)
+        del rp_d, col_d
+        return e, b
+
+    steps = max(1, min(args.steps, 3))
+    one_step()
+    torch.cuda.synchronize()
+    barrier(pg)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        e, b = one_step()
+        edges += e
+        d2h = b
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    dt = max_over_ranks(pg, dt, dev)
+    edges = sum_over_ranks(pg, float(edges), dev)
+    return {"value": edges / dt / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "steps": steps,
+            "timed": "host wall clock around pinned H2D of the CSR, slimsell_build, all runs with "
+                     "D2H of dist+parent, synchronised"}
+
+
+def ablations(ss, torch, g, roots, h_main, rp_d, col_d, args, stream, dev):
+    """Paper experiments on the same graph: sigma sweep, SlimWork off, SlimChunk off."""
+    n = g.n
+    out = {}
+    dist = torch.empty(n, dtype=torch.int32, device=dev)
+    parent = torch.empty(n, dtype=torch.int32, device=dev)
+
+    def measure(h, policy):
+        res = {}
+        for sr in SEMIRINGS:
+            ss.slimsell_bfs(h, int(roots[0]), SR_ID[sr], policy, dist, parent, stream)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            edges = 0
+            e0.record(stream)
+            for r in roots:
+                ss.slimsell_bfs(h, int(r), SR_ID[sr], policy, dist, parent, stream)
+                edges += ss.slimsell_get_run_stats(h)[0].reached_degree // 2
+            e1.record(stream)
+            torch.cuda.synchronize()
+            res[sr] = round(edges / (e0.elapsed_time(e1) / 1000.0) / 1e9, 3)
+        return res
+
+    out["sigma_n_slimwork"] = measure(h_main, ss.V_SLIMWORK)
+    out["sigma_n_no_slimwork"] = measure(h_main, ss.V_FULL)
+    for label, sigma, w in [("sigma_1024", 1024, args.split_w), ("sigma_1", 1, args.split_w),
+                            ("sigma_n_no_slimchunk", n, 0)]:
+        h = ss.slimsell_build(rp_d, col_d, n, g.nnz, 32, sigma, w, stream)
+        inf = ss.slimsell_get_info(h)
+        out[label] = measure(h, ss.V_SLIMWORK)
+        out[label + "_padding"] = int(inf.padding)
+        ss.slimsell_destroy(h)
+    out["roots"] = len(roots)
+    out["unit"] = "GTEPS"
+    return out
+
+
+if __name__ == "__main__":
+    main()
