@@ -153,6 +153,35 @@ ss_status slimsell_set_profiling(slimsell_handle h, int32_t on);
 ss_status slimsell_export_layout(slimsell_handle h, int32_t* d_perm, int32_t* d_cl, int64_t* d_cs,
                                  int32_t* d_col, int32_t* d_items, void* stream);
 
+/*
+ * Allocation-free sigma-window degree sort (the paper has no counterpart; this
+ * is a library convenience).  Writes perm[r] = the vertex placed at row
+ * position r by the same ordering slimsell_build uses (descending degree inside
+ * windows of sigma consecutive vertices, ties by ascending id; sigma <= 1 keeps
+ * the input order), for r in [0, n).
+ *
+ * For callers that must not allocate device memory: processes whose device
+ * memory is fully reserved by another allocator, where cudaMalloc would fail,
+ * and latency-bound loops that cannot accept the implicit synchronisation and
+ * unpredictable cost of cudaMalloc/cudaFree.  This call performs no device
+ * allocation and no freeing.  Its scratch is one fixed device array of about
+ * 12.3 MiB that every GPU loading the library holds until the process exits.
+ *   d_row_ptr  int64[n + 1] CSR offsets (degrees must be below n, i.e. no
+ *              duplicate entries or self-loops), device memory, not modified.
+ *   n          1 <= n <= 524288 (2^19); larger n returns SS_ERR_INVALID.
+ *   sigma      >= 1.
+ *   d_perm     int32[n] output, device memory owned by the caller.
+ * Stream-ordered and asynchronous: it returns after queueing its kernels.  The
+ * first call on a device looks up the array's device address (once per device,
+ * with that device current); make that first call before any stream capture.
+ * All calls share the one array and it keeps the last call's contents: calls
+ * that overlap on the GPU (different streams, or different host threads
+ * without ordering) race and corrupt each other's results, so order them.
+ * Errors: SS_ERR_INVALID (NULL pointers, n out of range, sigma < 1), SS_ERR_CUDA.
+ */
+ss_status slimsell_sigma_sort_noalloc(const int64_t* d_row_ptr, int32_t n, int32_t sigma,
+                                      int32_t* d_perm, void* stream);
+
 /* Free the handle and its device buffers (NULL is ignored). */
 void slimsell_destroy(slimsell_handle h);
 

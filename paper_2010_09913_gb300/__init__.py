@@ -73,6 +73,7 @@ def lib():
         "slimsell_set_profiling": (i32, [_VP, i32]),
         "slimsell_export_layout": (i32, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
         "slimsell_destroy": (None, [_VP]),
+        "slimsell_sigma_sort_noalloc": (i32, [_VP, i32, i32, _VP, _VP]),
         "slimsell_last_error": (ctypes.c_char_p, []),
         "slimsell_version": (ctypes.c_char_p, []),
     }
@@ -87,6 +88,7 @@ def lib():
 def exported_symbols() -> list[str]:
     return ["slimsell_build", "slimsell_bfs", "slimsell_get_info", "slimsell_get_run_stats",
             "slimsell_set_profiling", "slimsell_export_layout", "slimsell_destroy",
+            "slimsell_sigma_sort_noalloc",
             "slimsell_last_error", "slimsell_version"]
 
 
@@ -148,6 +150,14 @@ def slimsell_export_layout(h: int, perm, cl, cs, col, items, stream=None) -> Non
     _check("slimsell_export_layout", lib().slimsell_export_layout(
         h, _ptr(perm, torch.int32, "perm"), _ptr(cl, torch.int32, "cl"), _ptr(cs, torch.int64, "cs"),
         _ptr(col, torch.int32, "col"), _ptr(items, torch.int32, "items"), _stream(stream)))
+
+
+def slimsell_sigma_sort_noalloc(row_ptr: torch.Tensor, n: int, sigma: int, perm: torch.Tensor,
+                                stream=None) -> None:
+    """Allocation-free degree sort; see include/slimsell.h for its limits."""
+    _check("slimsell_sigma_sort_noalloc", lib().slimsell_sigma_sort_noalloc(
+        _ptr(row_ptr, torch.int64, "row_ptr"), int(n), int(sigma), _ptr(perm, torch.int32, "perm"),
+        _stream(stream)))
 
 
 def slimsell_destroy(h: int) -> None:

@@ -10,7 +10,7 @@
 #include <cstring>
 #include <vector>
 
-#include "ss_common.cuh"
+#include "ss_sort.cuh"
 
 namespace ss {
 
@@ -44,9 +44,6 @@ ss_status dmalloc(slimsell_graph* h, void** p, size_t bytes) {
 // ---------------------------------------------------------------------------
 // Exclusive prefix sum over int64 (three passes: tile sums, scan of sums, tile scans)
 // ---------------------------------------------------------------------------
-constexpr int SCAN_THREADS = 256;
-constexpr int SCAN_ITEMS = 16;
-constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 
 __device__ __forceinline__ long long warp_incl_scan(long long v) {
   const int lane = threadIdx.x & 31;
@@ -144,7 +141,7 @@ __global__ void k_tile_scan(const long long* in, long long* out, long long n, co
 }
 
 // exclusive scan of n int64 values in place; `tmp` must hold ceil(n / SCAN_TILE) entries
-static ss_status excl_scan(long long* data, long long n, long long* tmp, cudaStream_t st) {
+ss_status excl_scan(long long* data, long long n, long long* tmp, cudaStream_t st) {
   if (n <= 0) return SS_OK;
   long long ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
   k_tile_sum<<<(unsigned)ntiles, SCAN_THREADS, 0, st>>>(data, n, tmp);
@@ -157,9 +154,6 @@ static ss_status excl_scan(long long* data, long long n, long long* tmp, cudaStr
 // ---------------------------------------------------------------------------
 // Stable LSD radix sort of (uint64 key, int32 value), 8-bit digits
 // ---------------------------------------------------------------------------
-constexpr int RS_THREADS = 256;
-constexpr int RS_ITEMS = 16;
-constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
 
 __global__ void k_rs_hist(const unsigned long long* keys, int n, int shift, long long* hist, int nblk) {
   __shared__ unsigned h[256];
