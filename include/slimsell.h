@@ -140,6 +140,18 @@ ss_status slimsell_get_info(slimsell_handle h, ss_info* out);
 ss_status slimsell_get_run_stats(slimsell_handle h, ss_run_stats* out, ss_iter_stats* h_iters,
                                  int32_t cap);
 
+/* Options for slimsell_set_option. */
+typedef enum {
+  SS_OPT_DP_PASS = 1,     /* 1: tropical/real/boolean parents by a separate DP pass after the
+                             iterations (Section II-C as written); 0 (default): the same parents
+                             computed on the fly inside the iterations                        */
+  SS_OPT_SMEM_BYTES = 2   /* bytes of the frontier bitmap staged in shared memory per block,
+                             0 .. 212992 (default 212992); results do not depend on it          */
+} ss_option;
+
+/* Set a handle option (applies to later calls).  Errors: SS_ERR_INVALID. */
+ss_status slimsell_set_option(slimsell_handle h, int32_t option, int64_t value);
+
 /* Record CUDA events around the iteration kernels of later calls (0 = off). */
 ss_status slimsell_set_profiling(slimsell_handle h, int32_t on);
 

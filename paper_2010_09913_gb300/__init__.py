@@ -71,6 +71,7 @@ def lib():
         "slimsell_get_run_stats": (i32, [_VP, ctypes.POINTER(ss_run_stats),
                                          ctypes.POINTER(ss_iter_stats), i32]),
         "slimsell_set_profiling": (i32, [_VP, i32]),
+        "slimsell_set_option": (i32, [_VP, i32, i64]),
         "slimsell_export_layout": (i32, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
         "slimsell_destroy": (None, [_VP]),
         "slimsell_sigma_sort_noalloc": (i32, [_VP, i32, i32, _VP, _VP]),
@@ -87,7 +88,8 @@ def lib():
 
 def exported_symbols() -> list[str]:
     return ["slimsell_build", "slimsell_bfs", "slimsell_get_info", "slimsell_get_run_stats",
-            "slimsell_set_profiling", "slimsell_export_layout", "slimsell_destroy",
+            "slimsell_set_profiling", "slimsell_set_option", "slimsell_export_layout",
+            "slimsell_destroy",
             "slimsell_sigma_sort_noalloc",
             "slimsell_last_error", "slimsell_version"]
 
@@ -146,6 +148,13 @@ def slimsell_set_profiling(h: int, on: bool) -> None:
     _check("slimsell_set_profiling", lib().slimsell_set_profiling(h, 1 if on else 0))
 
 
+OPT_DP_PASS, OPT_SMEM_BYTES = 1, 2
+
+
+def slimsell_set_option(h: int, option: int, value: int) -> None:
+    _check("slimsell_set_option", lib().slimsell_set_option(h, int(option), int(value)))
+
+
 def slimsell_export_layout(h: int, perm, cl, cs, col, items, stream=None) -> None:
     _check("slimsell_export_layout", lib().slimsell_export_layout(
         h, _ptr(perm, torch.int32, "perm"), _ptr(cl, torch.int32, "cl"), _ptr(cs, torch.int64, "cs"),
@@ -195,6 +204,9 @@ class SlimSellGraph:
 
     def info(self) -> ss_info:
         return slimsell_get_info(self.h)
+
+    def set_option(self, option: int, value: int) -> None:
+        slimsell_set_option(self.h, option, value)
 
     def bfs(self, root: int, semiring="tropical", policy="slimwork", dist=None, parent=None,
             want_parent: bool = True, stream=None):

@@ -2,84 +2,60 @@
 // SlimSell, Section III-C SlimWork, Section III-D SlimChunk, Section II-C DP).
 //
 // Vertex state lives in the relabelled row space of the layout:
-//   lvl[r]        level of row r (SS_INF while unvisited).  For the tropical
-//                 semiring lvl *is* f_{k-1}: iteration k reads neighbours with
-//                 lvl <= k-1 and writes k into newly reached rows, which readers
-//                 of the same iteration treat as infinity, so a single buffer
-//                 reproduces x_k = A' (x) f_{k-1} exactly.
-//   fb/fr/fx[k&1] the frontier f_k of the boolean (1 bit), real (fp32 value) and
-//                 sel-max (original id + 1) semirings, double-buffered by parity.
-//   par           sel-max parent vector p_k (original id + 1; 0 = none).
+//   lvl[r]      level of row r (SS_INF while unvisited); this is the distance
+//               vector d and, for the tropical semiring, the vector f itself.
+//   fb[k&1]     1-bit image of the frontier f_k (the rows that entered at level k),
+//               double-buffered by level parity.  Every semiring's f_{k-1} is zero
+//               outside this set, so x_k = A (x) f_{k-1} only needs the semiring
+//               value of the neighbours whose bit is set:
+//                 tropical  f^u + 1 = k          (f^u = k - 1 on the frontier; rows
+//                                                 with non-frontier visited neighbours
+//                                                 are visited themselves and keep f^v)
+//                 boolean   1
+//                 real      fr[u], the path count u carried into the frontier
+//                 sel-max   id(u) + 1
+//   fr[r]       real-semiring value of row r when it entered the frontier.
+//   par[r]      parent original id + 1 (0 = none): sel-max p_k, or the DP parent.
 //
-// One warp processes one work item (chunk i, columns [j0, j1)).  Each lane loads
-// 16-byte quads of col: a quad is 4 consecutive rows of one column, so lane l
-// always meets the same 4 rows 4*(l mod C/4) .. +3 and keeps 4 accumulators;
-// the lanes sharing rows are combined with xor-shuffles at the end of the item.
-// Split chunks (SlimChunk) combine partial rows with atomics in xacc; the last
-// item of the chunk to arrive runs the post-processing.
+// Neighbours are stored in descending original id, so the first frontier hit
+// of a row (in column order) is its largest-id frontier neighbour: that is the
+// sel-max value and, for the other semirings, the DP parent (Section II-C)
+// computed on the fly; a separate DP pass after the iterations is also kept.
+//
+// The bitmap is gathered once per slot.  Random global gathers cost about one
+// L1 cycle each, so each block first stages a prefix of the bitmap (the
+// degree-sorted hubs, which receive most edges) in shared memory and reads
+// the rest through the read-only path.
+//
+// One warp processes one work item (chunk i, columns [j0, j1)).  Each lane
+// loads 16-byte quads of col: a quad is 4 consecutive rows of one column, so
+// lane l always meets rows 4*(l mod C/4) .. +3; lanes sharing rows are combined
+// with xor-shuffles.  Split chunks (SlimChunk) combine partial rows with
+// atomics; the last item of a chunk to arrive runs the post-processing.
 #include "ss_common.cuh"
 
 namespace ss {
 
-// ---------------------------------------------------------------------------
-// semiring traits: accumulator, identity, combine, neighbour value, atomic
-// ---------------------------------------------------------------------------
-template <int SR> struct Semi;
+constexpr int PULL_THREADS = 1024;  // one block per SM, 32 warps
+constexpr int PULL_STEP = 4;        // int4 col loads in flight per lane (16 slots)
 
-template <> struct Semi<SS_TROPICAL> {  // (min, +): value of u is f^u + 1 if f^u <= k-1
-  using T = int;
-  static __device__ __forceinline__ T id() { return SS_INF; }
-  static __device__ __forceinline__ T op(T a, T b) { return min(a, b); }
-  static __device__ __forceinline__ T load(const Dev& d, int km1, int c) {
-    int t = d.lvl[c];
-    return ((unsigned)t <= (unsigned)km1) ? t + 1 : SS_INF;
-  }
-  static __device__ __forceinline__ bool found(T a) { return a != SS_INF; }
-  static __device__ __forceinline__ void atomic(unsigned* p, T v) { atomicMin((int*)p, v); }
-  static __device__ __forceinline__ unsigned bits(T v) { return (unsigned)v; }
-  static __device__ __forceinline__ T from_bits(unsigned b) { return (T)b; }
-};
-
-template <> struct Semi<SS_REAL> {  // (+, *): value of u is f^u (0 outside the frontier)
-  using T = float;
-  static __device__ __forceinline__ T id() { return 0.0f; }
-  static __device__ __forceinline__ T op(T a, T b) { return a + b; }
-  static __device__ __forceinline__ T load(const Dev& d, int km1, int c) {
-    return __ldg(d.fr[km1 & 1] + c);
-  }
-  static __device__ __forceinline__ bool found(T a) { return a != 0.0f; }
-  static __device__ __forceinline__ void atomic(unsigned* p, T v) { atomicAdd((float*)p, v); }
-  static __device__ __forceinline__ unsigned bits(T v) { return __float_as_uint(v); }
-  static __device__ __forceinline__ T from_bits(unsigned b) { return __uint_as_float(b); }
-};
-
-template <> struct Semi<SS_BOOLEAN> {  // (|, &): value of u is its frontier bit
-  using T = unsigned;
-  static __device__ __forceinline__ T id() { return 0u; }
-  static __device__ __forceinline__ T op(T a, T b) { return a | b; }
-  static __device__ __forceinline__ T load(const Dev& d, int km1, int c) {
-    return (__ldg(d.fb[km1 & 1] + (c >> 5)) >> (c & 31)) & 1u;
-  }
-  static __device__ __forceinline__ bool found(T a) { return a != 0u; }
-  static __device__ __forceinline__ void atomic(unsigned* p, T v) { atomicOr(p, v); }
-  static __device__ __forceinline__ unsigned bits(T v) { return v; }
-  static __device__ __forceinline__ T from_bits(unsigned b) { return b; }
-};
-
-template <> struct Semi<SS_SELMAX> {  // (max, *): value of u is its id + 1 if in the frontier
-  using T = int;
-  static __device__ __forceinline__ T id() { return 0; }
-  static __device__ __forceinline__ T op(T a, T b) { return max(a, b); }
-  static __device__ __forceinline__ T load(const Dev& d, int km1, int c) {
-    return __ldg(d.fx[km1 & 1] + c);
-  }
-  static __device__ __forceinline__ bool found(T a) { return a != 0; }
-  static __device__ __forceinline__ void atomic(unsigned* p, T v) { atomicMax((int*)p, v); }
-  static __device__ __forceinline__ unsigned bits(T v) { return (unsigned)v; }
-  static __device__ __forceinline__ T from_bits(unsigned b) { return (T)b; }
-};
+enum { MODE_FULL = 0, MODE_SLIMWORK = 1, MODE_FILTERED = 3 };
 
 __device__ __forceinline__ int4 ld_stream(const int4* p) { return __ldcs(p); }
+
+__device__ __forceinline__ int4 shfl_int4(int4 v, int src) {
+  return make_int4(__shfl_sync(SS_FULL_MASK, v.x, src), __shfl_sync(SS_FULL_MASK, v.y, src),
+                   __shfl_sync(SS_FULL_MASK, v.z, src), __shfl_sync(SS_FULL_MASK, v.w, src));
+}
+
+// Frontier bit of relabelled vertex c (c = -1 for padding gives 0).
+__device__ __forceinline__ unsigned frontier_bit(const unsigned* sm, int sbits, const unsigned* gbm,
+                                                 int c) {
+  unsigned w;
+  if ((unsigned)c < (unsigned)sbits) w = sm[c >> 5];
+  else w = (c >= 0) ? __ldg(gbm + (c >> 5)) : 0u;
+  return (w >> (c & 31)) & 1u;
+}
 
 // Store the C frontier bits of one chunk (bit l = row l) into the bitmap.
 template <int C>
@@ -107,174 +83,224 @@ struct Counters {
   unsigned long long nw = 0, deg = 0, slots = 0, act = 0;
 };
 
-// Post-process one chunk (Section III-A listing of the frontier update): derive
-// f_k, d and p from x_k = acc for rows R0 .. R0+3 owned by this lane (lane < Q),
-// write the next SlimWork state, count new vertices.  All lanes of the warp call.
+// Per-row result of one item: best = largest original id among frontier
+// neighbours (-1 if none) and, for the real semiring, the sum of their values.
+struct RowAcc {
+  int best[4];
+  float sum[4];
+};
+
+// Post-process one chunk (the frontier update of Section III-A): new rows are
+// the unvisited rows whose x_k is non-zero; they get level k, a parent and a
+// frontier bit; the chunk's SlimWork state is refreshed.  All lanes call.
 template <int SR, int C>
-__device__ __forceinline__ void post_chunk(const Dev& d, int k, int chunk, int lane,
-                                           const typename Semi<SR>::T acc[4], Counters& cnt) {
-  using S = Semi<SR>;
+__device__ __forceinline__ void post_chunk(const Dev& d, int k, int chunk, int lane, int4 lv,
+                                           const RowAcc& a, Counters& cnt) {
   constexpr int Q = C / 4;
-  const bool own = lane < Q;
   const int R0 = chunk * C + 4 * lane;
   unsigned nib = 0, left = 0;
-  if (own) {
-    int4 lv = *reinterpret_cast<const int4*>(d.lvl + R0);
+  if (lane < Q) {
     int L[4] = {lv.x, lv.y, lv.z, lv.w};
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-      bool unvisited = (L[r] == SS_INF);
-      bool nw = unvisited && S::found(acc[r]);
-      if (nw) nib |= 1u << r;
+      const bool unvisited = (L[r] == SS_INF);
+      const bool found = (SR == SS_REAL) ? (a.sum[r] != 0.0f) : (a.best[r] >= 0);
+      if (unvisited && found) nib |= 1u << r;
       else if (unvisited) left = 1;
     }
     if (nib) {
 #pragma unroll
       for (int r = 0; r < 4; ++r)
-        if (nib >> r & 1u) L[r] = k;
+        if (nib >> r & 1u) {
+          L[r] = k;
+          d.par[R0 + r] = a.best[r] + 1;  // p_k = p_{k-1} + not(p_{k-1}) (.) x_k / DP parent
+          if (SR == SS_REAL) d.fr[R0 + r] = a.sum[r];
+        }
       *reinterpret_cast<int4*>(d.lvl + R0) = make_int4(L[0], L[1], L[2], L[3]);
-      int4 dg = *reinterpret_cast<const int4*>(d.rdeg + R0);
-      int D[4] = {dg.x, dg.y, dg.z, dg.w};
+      const int4 dg = *reinterpret_cast<const int4*>(d.rdeg + R0);
+      const int D[4] = {dg.x, dg.y, dg.z, dg.w};
 #pragma unroll
       for (int r = 0; r < 4; ++r)
         if (nib >> r & 1u) cnt.deg += (unsigned long long)D[r];
       cnt.nw += __popc(nib);
     }
-    if (SR == SS_REAL) {
-      float4 f;
-      f.x = (nib & 1u) ? acc[0] : 0.0f;
-      f.y = (nib & 2u) ? acc[1] : 0.0f;
-      f.z = (nib & 4u) ? acc[2] : 0.0f;
-      f.w = (nib & 8u) ? acc[3] : 0.0f;
-      *reinterpret_cast<float4*>(d.fr[k & 1] + R0) = f;
-    } else if (SR == SS_SELMAX) {
-      int4 x = make_int4(0, 0, 0, 0);
-      if (nib) {
-        int4 pm = *reinterpret_cast<const int4*>(d.perm + R0);
-        int4 pv = *reinterpret_cast<const int4*>(d.par + R0);
-        // p_k = p_{k-1} + not(p_{k-1}) (.) x_k ; frontier carries the vertex ids
-        if (nib & 1u) { x.x = pm.x + 1; pv.x = (int)acc[0]; }
-        if (nib & 2u) { x.y = pm.y + 1; pv.y = (int)acc[1]; }
-        if (nib & 4u) { x.z = pm.z + 1; pv.z = (int)acc[2]; }
-        if (nib & 8u) { x.w = pm.w + 1; pv.w = (int)acc[3]; }
-        *reinterpret_cast<int4*>(d.par + R0) = pv;
-      }
-      *reinterpret_cast<int4*>(d.fx[k & 1] + R0) = x;
+  }
+  unsigned lo, hi;
+  gather_bits<C>(nib, lane, &lo, &hi);
+  const unsigned any_left = __any_sync(SS_FULL_MASK, left);
+  if (lane == 0) {
+    store_bits<C>(d.fb[k & 1], chunk, lo, hi);
+    d.act[chunk] = any_left ? 1 : 3;
+  }
+}
+
+// A skipped chunk (SlimWork) has only final rows, so f_k is zero there; its bits
+// in the parity buffer are cleared for the two iterations after its last
+// discovery (states 3 and 2), then left alone (state 0).
+template <int C>
+__device__ __forceinline__ void carry_chunk(const Dev& d, int k, int chunk, int lane, int a) {
+  if (a < 2) return;
+  if (lane == 0) {
+    store_bits<C>(d.fb[k & 1], chunk, 0u, 0u);
+    d.act[chunk] = (a == 3) ? 2 : 0;
+  }
+}
+
+// Scan the slots of one quad: record the first frontier hit per row and, for
+// the real semiring, add the values of all hits.
+template <int SR>
+__device__ __forceinline__ void scan_quad(const Dev& d, const unsigned* sm, int sbits,
+                                          const unsigned* gbm, int4 c, int first[4], float sum[4]) {
+  const int cc[4] = {c.x, c.y, c.z, c.w};
+  unsigned hit[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) hit[r] = frontier_bit(sm, sbits, gbm, cc[r]);
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    if (hit[r]) {
+      if (first[r] < 0) first[r] = cc[r];
+      if (SR == SS_REAL) sum[r] += __ldg(d.fr + cc[r]);
     }
   }
-  if (SR == SS_BOOLEAN) {
-    unsigned lo, hi;
-    gather_bits<C>(nib, lane, &lo, &hi);
-    if (lane == 0) store_bits<C>(d.fb[k & 1], chunk, lo, hi);
-  }
-  unsigned any_left = __any_sync(SS_FULL_MASK, left);
-  if (lane == 0) d.act[chunk] = any_left ? 1 : (SR == SS_TROPICAL ? 0 : 3);
 }
 
-// A skipped chunk (SlimWork) carries its values over: its rows are all final, so
-// f_k is zero there; clear the parity buffer for the two iterations after the
-// chunk's last discovery, then leave it alone.
-template <int SR, int C>
-__device__ __forceinline__ void carry_chunk(const Dev& d, int k, int chunk, int lane, unsigned char a) {
-  if (SR == SS_TROPICAL || a < 2) return;
-  constexpr int Q = C / 4;
-  const int R0 = chunk * C + 4 * lane;
-  if (SR == SS_BOOLEAN) {
-    if (lane == 0) store_bits<C>(d.fb[k & 1], chunk, 0u, 0u);
-  } else if (SR == SS_REAL) {
-    if (lane < Q) *reinterpret_cast<float4*>(d.fr[k & 1] + R0) = make_float4(0.f, 0.f, 0.f, 0.f);
-  } else {
-    if (lane < Q) *reinterpret_cast<int4*>(d.fx[k & 1] + R0) = make_int4(0, 0, 0, 0);
-  }
-  if (lane == 0) d.act[chunk] = (a == 3) ? 2 : 0;
-}
-
-template <int SR>
-__device__ __forceinline__ void acc_quad(const Dev& d, int km1, int4 c, typename Semi<SR>::T acc[4]) {
-  using S = Semi<SR>;
-  if (c.x >= 0) acc[0] = S::op(acc[0], S::load(d, km1, c.x));
-  if (c.y >= 0) acc[1] = S::op(acc[1], S::load(d, km1, c.y));
-  if (c.z >= 0) acc[2] = S::op(acc[2], S::load(d, km1, c.z));
-  if (c.w >= 0) acc[3] = S::op(acc[3], S::load(d, km1, c.w));
-}
-
-constexpr int PULL_THREADS = 256;
-constexpr int PULL_UNROLL = 2;
+extern __shared__ __align__(16) unsigned ss_smem_bits[];
 
 // One frontier expansion x_k = A (x)_S f_{k-1} with fused post-processing.
-template <int SR, int C, bool SLIMWORK>
-__global__ void __launch_bounds__(PULL_THREADS) k_pull(Dev d) {
-  using S = Semi<SR>;
-  using T = typename S::T;
+// Warp w of the grid owns items w, w + W, w + 2W, ... (W = warps in the grid,
+// the item list is ordered for that assignment); it reads the descriptors and
+// SlimWork states of 32 of them at once (one per lane) and walks the active ones.
+template <int SR, int C, int MODE>
+__global__ void __launch_bounds__(PULL_THREADS, 1) k_pull(Dev d) {
   constexpr int Q = C / 4;
   if (d.ctl->done) return;
   const int k = d.ctl->k;
   const int km1 = k - 1;
   const int lane = threadIdx.x & 31;
-  const int wid = (blockIdx.x * PULL_THREADS + threadIdx.x) >> 5;
-  const int nw = (gridDim.x * PULL_THREADS) >> 5;
+  const int wid = blockIdx.x * (PULL_THREADS / 32) + (threadIdx.x >> 5);
+  const int nw = gridDim.x * (PULL_THREADS / 32);
+  const unsigned* gbm = d.fb[km1 & 1];
+  // stage the bitmap prefix of f_{k-1}
+  const int sw = d.smem_words;
+  for (int i = threadIdx.x; i < (sw >> 2); i += PULL_THREADS)
+    reinterpret_cast<int4*>(ss_smem_bits)[i] = __ldg(reinterpret_cast<const int4*>(gbm) + i);
+  __syncthreads();
+  const unsigned* sm = ss_smem_bits;
+  const int sbits = sw * 32;
   Counters cnt;
-  for (int it = wid; it < d.n_items; it += nw) {
-    const int4 item = d.items[it];
-    const int chunk = item.x;
-    if (SLIMWORK) {
-      unsigned char a = d.act[chunk];
-      if (a != 1) {
-        if (item.y == 0) carry_chunk<SR, C>(d, k, chunk, lane, a);
-        continue;
+  unsigned long long lane_slots = 0;
+  for (long long b0 = wid; b0 < d.n_items; b0 += 32LL * nw) {
+    const long long my_it = b0 + (long long)lane * nw;
+    int4 my_item = make_int4(0, 0, 0, -1);
+    long long my_start = 0;
+    int a = 0;
+    if (my_it < d.n_items) {
+      my_item = d.items[my_it];
+      a = (MODE == MODE_FULL) ? 1 : d.act[my_item.x];
+      my_start = d.cs[my_item.x] + (long long)my_item.y * C;
+    }
+    unsigned todo = __ballot_sync(SS_FULL_MASK, a == 1);
+    if (MODE != MODE_FULL) {
+      unsigned carry = __ballot_sync(SS_FULL_MASK, a >= 2 && my_item.y == 0);
+      while (carry) {
+        const int src = __ffs(carry) - 1;
+        carry &= carry - 1;
+        carry_chunk<C>(d, k, __shfl_sync(SS_FULL_MASK, my_item.x, src), lane,
+                       __shfl_sync(SS_FULL_MASK, a, src));
       }
     }
-    T acc[4] = {S::id(), S::id(), S::id(), S::id()};
-    const int nq = (item.z - item.y) * Q;
-    const int4* base = reinterpret_cast<const int4*>(d.col + d.cs[chunk] + (long long)item.y * C);
-    int q = lane;
-    for (; q + 32 * (PULL_UNROLL - 1) < nq; q += 32 * PULL_UNROLL) {
-      int4 c[PULL_UNROLL];
+    while (todo) {
+      const int src = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const int4 item = shfl_int4(my_item, src);
+      const long long start = __shfl_sync(SS_FULL_MASK, my_start, src);
+      const int chunk = item.x;
+      // levels of this lane's 4 rows (prefetched; only this chunk's post writes them)
+      const int4 lv = *reinterpret_cast<const int4*>(d.lvl + chunk * C + 4 * (lane % Q));
+      const int L[4] = {lv.x, lv.y, lv.z, lv.w};
+      int first[4] = {-1, -1, -1, -1};
+      float sum[4] = {0.f, 0.f, 0.f, 0.f};
+      bool need = true;
+      if (MODE == MODE_FILTERED) {  // only unvisited rows are computed
+        need = false;
 #pragma unroll
-      for (int u = 0; u < PULL_UNROLL; ++u) c[u] = ld_stream(base + q + 32 * u);
-#pragma unroll
-      for (int u = 0; u < PULL_UNROLL; ++u) acc_quad<SR>(d, km1, c[u], acc);
-    }
-    for (; q < nq; q += 32) acc_quad<SR>(d, km1, ld_stream(base + q), acc);
-    // lanes with equal lane mod Q hold partial results of the same rows
-#pragma unroll
-    for (int off = Q; off < 32; off <<= 1) {
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        if (SR == SS_REAL) acc[r] = S::op(acc[r], __shfl_xor_sync(SS_FULL_MASK, acc[r], off));
-        else acc[r] = S::op(acc[r], (T)__shfl_xor_sync(SS_FULL_MASK, (int)acc[r], off));
+        for (int r = 0; r < 4; ++r) need |= (L[r] == SS_INF);
       }
-    }
-    if (lane == 0) cnt.slots += (unsigned long long)(item.z - item.y) * C;
-    if (item.w >= 0) {  // SlimChunk: combine partial rows, the last arriving item post-processes
-      unsigned* xa = d.xacc + (size_t)item.w * C + 4 * lane;
-      if (lane < Q) {
+      const int nq = (item.z - item.y) * Q;
+      const int4* base = reinterpret_cast<const int4*>(d.col + start);
+      for (int q0 = 0; q0 < nq; q0 += 32 * PULL_STEP) {
+        if (MODE == MODE_FILTERED) {
+          if (!__any_sync(SS_FULL_MASK, need)) break;
+          if (!need) continue;
+        }
+        int4 c[PULL_STEP];
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
-          if (S::found(acc[r])) S::atomic(xa + r, acc[r]);
-        __threadfence();
-      }
-      __syncwarp();
-      int last = 0;
-      if (lane == 0) {
-        unsigned old = atomicAdd(d.arrive + item.w, 1u);
-        last = (old == (unsigned)d.split_n[item.w] - 1u);
-      }
-      last = __shfl_sync(SS_FULL_MASK, last, 0);
-      if (!last) continue;
-      __threadfence();
-      if (lane < Q) {
+        for (int u = 0; u < PULL_STEP; ++u) {
+          const int q = q0 + lane + 32 * u;
+          c[u] = (q < nq) ? ld_stream(base + q) : make_int4(-1, -1, -1, -1);
+          if (MODE == MODE_FILTERED && q < nq) lane_slots += 4;
+        }
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          acc[r] = S::from_bits(__ldcg(xa + r));
-          xa[r] = S::bits(S::id());
+        for (int u = 0; u < PULL_STEP; ++u) scan_quad<SR>(d, sm, sbits, gbm, c[u], first, sum);
+        if (MODE == MODE_FILTERED) {  // a row is done once visited or (not real) hit
+          need = false;
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+            need |= (L[r] == SS_INF) && (SR == SS_REAL || first[r] < 0);
         }
       }
-      if (lane == 0) d.arrive[item.w] = 0u;
+      if (MODE != MODE_FILTERED && lane == 0) cnt.slots += (unsigned long long)(item.z - item.y) * C;
+      // the largest original id among this lane's first hits of unvisited rows
+      RowAcc acc;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        acc.best[r] = (first[r] >= 0 && L[r] == SS_INF) ? __ldg(d.perm + first[r]) : -1;
+        acc.sum[r] = sum[r];
+      }
+#pragma unroll
+      for (int off = Q; off < 32; off <<= 1)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          acc.best[r] = max(acc.best[r], __shfl_xor_sync(SS_FULL_MASK, acc.best[r], off));
+          if (SR == SS_REAL) acc.sum[r] += __shfl_xor_sync(SS_FULL_MASK, acc.sum[r], off);
+        }
+      if (item.w >= 0) {  // SlimChunk: combine partial rows, the last arriving item post-processes
+        const size_t xo = (size_t)item.w * C + 4 * lane;
+        if (lane < Q) {
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            if (acc.best[r] >= 0) atomicMax(d.xpar + xo + r, acc.best[r]);
+            if (SR == SS_REAL && acc.sum[r] != 0.0f) atomicAdd(d.xacc + xo + r, acc.sum[r]);
+          }
+          __threadfence();
+        }
+        __syncwarp();
+        int last = 0;
+        if (lane == 0) {
+          const unsigned old = atomicAdd(d.arrive + item.w, 1u);
+          last = (old == (unsigned)d.split_n[item.w] - 1u);
+        }
+        last = __shfl_sync(SS_FULL_MASK, last, 0);
+        if (!last) continue;
+        __threadfence();
+        if (lane < Q) {
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            acc.best[r] = __ldcg(d.xpar + xo + r);
+            d.xpar[xo + r] = -1;
+            if (SR == SS_REAL) {
+              acc.sum[r] = __ldcg(d.xacc + xo + r);
+              d.xacc[xo + r] = 0.0f;
+            }
+          }
+        }
+        if (lane == 0) d.arrive[item.w] = 0u;
+      }
+      if (lane == 0) cnt.act += 1;
+      post_chunk<SR, C>(d, k, chunk, lane, lv, acc, cnt);
     }
-    if (lane == 0) cnt.act += 1;
-    post_chunk<SR, C>(d, k, chunk, lane, acc, cnt);
   }
+  if (MODE == MODE_FILTERED) cnt.slots = lane_slots;
   // warp, then block reduction of the counters; one atomic per block and counter
   __shared__ unsigned long long red[4][PULL_THREADS / 32];
   unsigned long long v[4] = {cnt.nw, cnt.deg, cnt.slots, cnt.act};
@@ -326,29 +352,27 @@ __global__ void k_tail(Dev d, int variant) {
   c->k = k + 1;
 }
 
-__global__ void k_init(Dev d, int sr) {
+__global__ void k_init(Dev d) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  for (long long r = t0; r < d.n_pad; r += stride) {
-    d.lvl[r] = r < d.n ? SS_INF : SS_PAD_LEVEL;
-    if (sr == SS_REAL) { d.fr[0][r] = 0.0f; d.fr[1][r] = 0.0f; }
-    if (sr == SS_SELMAX) { d.fx[0][r] = 0; d.fx[1][r] = 0; d.par[r] = 0; }
-  }
-  if (sr == SS_BOOLEAN) {
-    const long long words = ((long long)d.n_pad + 31) / 32;
-    for (long long w = t0; w < words; w += stride) { d.fb[0][w] = 0u; d.fb[1][w] = 0u; }
+  for (long long r = t0; r < d.n_pad; r += stride) d.lvl[r] = r < d.n ? SS_INF : SS_PAD_LEVEL;
+  for (long long w = t0; w < d.fb_words; w += stride) {
+    d.fb[0][w] = 0u;
+    d.fb[1][w] = 0u;
   }
   for (long long i = t0; i < d.n_c; i += stride) d.act[i] = 1;
-  const unsigned ident = (sr == SS_TROPICAL) ? (unsigned)SS_INF : 0u;
-  for (long long s = t0; s < (long long)d.n_split * d.C; s += stride) d.xacc[s] = ident;
+  for (long long s = t0; s < (long long)d.n_split * d.C; s += stride) {
+    d.xacc[s] = 0.0f;
+    d.xpar[s] = -1;
+  }
 }
 
-__global__ void k_init_root(Dev d, int sr, int root) {
+__global__ void k_init_root(Dev d, int root) {
   const int r = d.invperm[root];
   d.lvl[r] = 0;
-  if (sr == SS_BOOLEAN) d.fb[0][r >> 5] |= 1u << (r & 31);
-  if (sr == SS_REAL) d.fr[0][r] = 1.0f;
-  if (sr == SS_SELMAX) { d.fx[0][r] = root + 1; d.par[r] = root + 1; }
+  d.fb[0][r >> 5] |= 1u << (r & 31);
+  d.fr[r] = 1.0f;
+  d.par[r] = root + 1;
   Ctl* c = d.ctl;
   c->k = 1; c->done = 0; c->error = 0; c->variant = -1;
   c->new_count = 0; c->new_deg = 0; c->slots = 0; c->active = 0;
@@ -360,61 +384,90 @@ __global__ void k_init_root(Dev d, int sr, int root) {
   d.iters[0] = s;
 }
 
-// DP transformation (Section II-C): the parent of a row at level L >= 1 is its
-// largest-id neighbour at level L-1.  Neighbours are stored in descending
-// original id, so each lane's first hit in its column sequence is that lane's
-// maximum; lanes stop once their rows are resolved and the group takes the max.
+// DP transformation as a separate pass (Section II-C): the parent of a row at
+// level L >= 1 is its largest-id neighbour at level L-1.  Neighbours are stored
+// in descending original id, so each lane's first hit in its column sequence is
+// that lane's maximum; lanes stop once their rows are resolved.
 template <int C>
-__global__ void __launch_bounds__(PULL_THREADS) k_dp(Dev d) {
+__global__ void __launch_bounds__(PULL_THREADS, 1) k_dp(Dev d) {
   constexpr int Q = C / 4;
   const int lane = threadIdx.x & 31;
-  const int wid = (blockIdx.x * PULL_THREADS + threadIdx.x) >> 5;
-  const int nw = (gridDim.x * PULL_THREADS) >> 5;
+  const int wid = blockIdx.x * (PULL_THREADS / 32) + (threadIdx.x >> 5);
+  const int nw = gridDim.x * (PULL_THREADS / 32);
   unsigned long long my_slots = 0;
-  for (int it = wid; it < d.n_items; it += nw) {
-    const int4 item = d.items[it];
-    const int chunk = item.x;
-    const int R0 = chunk * C + 4 * (lane % Q);
-    int4 lv = *reinterpret_cast<const int4*>(d.lvl + R0);
-    int tgt[4] = {lv.x, lv.y, lv.z, lv.w};
-    int best[4];
-    bool need = false;
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      tgt[r] = (tgt[r] >= 1 && tgt[r] != SS_INF) ? tgt[r] - 1 : -2;
-      best[r] = -1;
-      need |= tgt[r] >= 0;
+  for (long long b0 = wid; b0 < d.n_items; b0 += 32LL * nw) {
+    const long long my_it = b0 + (long long)lane * nw;
+    int4 my_item = make_int4(0, 0, 0, -1);
+    long long my_start = 0;
+    if (my_it < d.n_items) {
+      my_item = d.items[my_it];
+      my_start = d.cs[my_item.x] + (long long)my_item.y * C;
     }
-    const int nq = (item.z - item.y) * Q;
-    const int4* base = reinterpret_cast<const int4*>(d.col + d.cs[chunk] + (long long)item.y * C);
-    int q = lane;
-    while (__any_sync(SS_FULL_MASK, need && q < nq)) {
-      if (need && q < nq) {
-        int4 c = ld_stream(base + q);
-        int cc[4] = {c.x, c.y, c.z, c.w};
+    unsigned todo = __ballot_sync(SS_FULL_MASK, my_it < d.n_items);
+    while (todo) {
+      const int src = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const int4 item = shfl_int4(my_item, src);
+      const long long start = __shfl_sync(SS_FULL_MASK, my_start, src);
+      const int chunk = item.x;
+      const int R0 = chunk * C + 4 * (lane % Q);
+      const int4 lv = *reinterpret_cast<const int4*>(d.lvl + R0);
+      int tgt[4] = {lv.x, lv.y, lv.z, lv.w};
+      int hit[4];
+      bool need = false;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        tgt[r] = (tgt[r] >= 1 && tgt[r] != SS_INF) ? tgt[r] - 1 : -2;
+        hit[r] = -1;
+        need |= tgt[r] >= 0;
+      }
+      const int nq = (item.z - item.y) * Q;
+      const int4* base = reinterpret_cast<const int4*>(d.col + start);
+      for (int q0 = 0; q0 < nq && __any_sync(SS_FULL_MASK, need); q0 += 32 * PULL_STEP) {
+        if (!need) continue;
+        int4 c[PULL_STEP];
+#pragma unroll
+        for (int u = 0; u < PULL_STEP; ++u) {
+          const int q = q0 + lane + 32 * u;
+          c[u] = (q < nq) ? ld_stream(base + q) : make_int4(-1, -1, -1, -1);
+          if (q < nq) my_slots += 4;
+        }
+        int Lv[PULL_STEP][4];
+#pragma unroll
+        for (int u = 0; u < PULL_STEP; ++u) {
+          Lv[u][0] = d.lvl[max(c[u].x, 0)];
+          Lv[u][1] = d.lvl[max(c[u].y, 0)];
+          Lv[u][2] = d.lvl[max(c[u].z, 0)];
+          Lv[u][3] = d.lvl[max(c[u].w, 0)];
+        }
         need = false;
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          if (best[r] < 0 && tgt[r] >= 0) {
-            if (cc[r] >= 0 && d.lvl[cc[r]] == tgt[r]) best[r] = d.perm[cc[r]];
-            else need = true;
-          }
+        for (int u = 0; u < PULL_STEP; ++u) {
+          const int cc[4] = {c[u].x, c[u].y, c[u].z, c[u].w};
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+            if (hit[r] < 0 && tgt[r] >= 0 && cc[r] >= 0 && Lv[u][r] == tgt[r]) hit[r] = cc[r];
         }
-        q += 32;
-        my_slots += 4;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) need |= (tgt[r] >= 0 && hit[r] < 0);
       }
-    }
+      int best[4];
 #pragma unroll
-    for (int off = Q; off < 32; off <<= 1)
+      for (int r = 0; r < 4; ++r) best[r] = hit[r] >= 0 ? d.perm[hit[r]] : -1;
 #pragma unroll
-      for (int r = 0; r < 4; ++r) best[r] = max(best[r], __shfl_xor_sync(SS_FULL_MASK, best[r], off));
-    if (lane < Q) {
-      if (item.w < 0) {
-        *reinterpret_cast<int4*>(d.par + R0) = make_int4(best[0], best[1], best[2], best[3]);
-      } else {
+      for (int off = Q; off < 32; off <<= 1)
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
-          if (best[r] >= 0) atomicMax(d.par + R0 + r, best[r]);
+        for (int r = 0; r < 4; ++r) best[r] = max(best[r], __shfl_xor_sync(SS_FULL_MASK, best[r], off));
+      if (lane < Q) {
+        if (item.w < 0) {
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+            if (tgt[r] >= 0) d.par[R0 + r] = best[r] + 1;
+        } else {
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+            if (best[r] >= 0) atomicMax(d.par + R0 + r, best[r] + 1);
+        }
       }
     }
   }
@@ -430,78 +483,82 @@ __global__ void __launch_bounds__(PULL_THREADS) k_dp(Dev d) {
   }
 }
 
-__global__ void k_output(Dev d, int* dist, int* parent, int selmax) {
+// Rows of split chunks start the DP pass at "no parent" (they combine by atomicMax).
+__global__ void k_dp_clear(Dev d) {
+  for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < d.n_items;
+       it += (long long)gridDim.x * blockDim.x) {
+    const int4 item = d.items[it];
+    if (item.w >= 0 && item.y == 0)
+      for (int l = 0; l < d.C; ++l)
+        if (d.lvl[item.x * d.C + l] >= 1) d.par[item.x * d.C + l] = 0;
+  }
+}
+
+__global__ void k_output(Dev d, int* dist, int* parent) {
   for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < d.n;
        v += (long long)gridDim.x * blockDim.x) {
     const int r = d.invperm[v];
     const int L = d.lvl[r];
     if (dist) dist[v] = (L == SS_INF) ? -1 : L;
-    if (parent) {
-      int p;
-      if (L == SS_INF) p = -1;
-      else if (L == 0) p = (int)v;
-      else p = selmax ? d.par[r] - 1 : d.par[r];
-      parent[v] = p;
-    }
+    if (parent) parent[v] = (L == SS_INF) ? -1 : d.par[r] - 1;
   }
 }
 
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-template <typename K>
-static int grid_for(K kernel, int num_sms) {
-  int blocks = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, PULL_THREADS, 0);
-  if (blocks < 1) blocks = 1;
-  return blocks * num_sms;
-}
-
-template <int SR, int C>
-static ss_status launch_pull(const slimsell_graph* h, const Dev& d, bool slimwork, cudaStream_t st) {
-  if (slimwork) {
-    static int g = 0;
-    if (!g) g = grid_for(k_pull<SR, C, true>, h->num_sms);
-    k_pull<SR, C, true><<<g, PULL_THREADS, 0, st>>>(d);
-  } else {
-    static int g = 0;
-    if (!g) g = grid_for(k_pull<SR, C, false>, h->num_sms);
-    k_pull<SR, C, false><<<g, PULL_THREADS, 0, st>>>(d);
+template <int SR, int C, int MODE>
+static ss_status launch_pull(const slimsell_graph* h, const Dev& d, cudaStream_t st) {
+  static bool configured = false;
+  if (!configured) {
+    SS_CUDA(cudaFuncSetAttribute(k_pull<SR, C, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 SS_SMEM_MAX_BYTES));
+    configured = true;
   }
+  k_pull<SR, C, MODE><<<h->num_sms, PULL_THREADS, (size_t)d.smem_words * 4, st>>>(d);
   SS_CUDA(cudaGetLastError());
   return SS_OK;
 }
 
-template <int SR>
-static ss_status launch_pull_c(const slimsell_graph* h, const Dev& d, bool slimwork, cudaStream_t st) {
+template <int SR, int MODE>
+static ss_status launch_pull_c(const slimsell_graph* h, const Dev& d, cudaStream_t st) {
   switch (h->C) {
-    case 8: return launch_pull<SR, 8>(h, d, slimwork, st);
-    case 16: return launch_pull<SR, 16>(h, d, slimwork, st);
-    case 32: return launch_pull<SR, 32>(h, d, slimwork, st);
-    default: return launch_pull<SR, 64>(h, d, slimwork, st);
+    case 8: return launch_pull<SR, 8, MODE>(h, d, st);
+    case 16: return launch_pull<SR, 16, MODE>(h, d, st);
+    case 32: return launch_pull<SR, 32, MODE>(h, d, st);
+    default: return launch_pull<SR, 64, MODE>(h, d, st);
   }
 }
 
-static ss_status launch_iteration(const slimsell_graph* h, const Dev& d, int sr, bool slimwork,
+template <int SR>
+static ss_status launch_pull_m(const slimsell_graph* h, const Dev& d, int mode, cudaStream_t st) {
+  switch (mode) {
+    case MODE_FULL: return launch_pull_c<SR, MODE_FULL>(h, d, st);
+    case MODE_SLIMWORK: return launch_pull_c<SR, MODE_SLIMWORK>(h, d, st);
+    default: return launch_pull_c<SR, MODE_FILTERED>(h, d, st);
+  }
+}
+
+static ss_status launch_iteration(const slimsell_graph* h, const Dev& d, int sr, int mode,
                                   cudaStream_t st) {
   switch (sr) {
-    case SS_TROPICAL: return launch_pull_c<SS_TROPICAL>(h, d, slimwork, st);
-    case SS_REAL: return launch_pull_c<SS_REAL>(h, d, slimwork, st);
-    case SS_BOOLEAN: return launch_pull_c<SS_BOOLEAN>(h, d, slimwork, st);
-    default: return launch_pull_c<SS_SELMAX>(h, d, slimwork, st);
+    case SS_TROPICAL: return launch_pull_m<SS_TROPICAL>(h, d, mode, st);
+    case SS_REAL: return launch_pull_m<SS_REAL>(h, d, mode, st);
+    case SS_BOOLEAN: return launch_pull_m<SS_BOOLEAN>(h, d, mode, st);
+    default: return launch_pull_m<SS_SELMAX>(h, d, mode, st);
   }
 }
 
 template <int C>
 static ss_status launch_dp_c(const slimsell_graph* h, const Dev& d, cudaStream_t st) {
-  static int g = 0;
-  if (!g) g = grid_for(k_dp<C>, h->num_sms);
-  k_dp<C><<<g, PULL_THREADS, 0, st>>>(d);
+  k_dp<C><<<h->num_sms, PULL_THREADS, 0, st>>>(d);
   SS_CUDA(cudaGetLastError());
   return SS_OK;
 }
 
 static ss_status launch_dp(const slimsell_graph* h, const Dev& d, cudaStream_t st) {
+  k_dp_clear<<<4 * h->num_sms, 256, 0, st>>>(d);
+  SS_CUDA(cudaGetLastError());
   switch (h->C) {
     case 8: return launch_dp_c<8>(h, d, st);
     case 16: return launch_dp_c<16>(h, d, st);
@@ -534,20 +591,23 @@ ss_status slimsell_bfs(slimsell_handle h, int32_t root, int32_t semiring, int32_
     set_error("slimsell_bfs: unknown policy %d", policy);
     return SS_ERR_INVALID;
   }
-  if (policy != SS_V_FULL && policy != SS_V_SLIMWORK) {
+  int mode;
+  if (policy == SS_V_FULL) mode = MODE_FULL;
+  else if (policy == SS_V_SLIMWORK) mode = MODE_SLIMWORK;
+  else if (policy == SS_V_PULL_FILTERED) mode = MODE_FILTERED;
+  else {
     set_error("slimsell_bfs: policy %d not available in this build", policy);
     return SS_ERR_UNSUPPORTED;
   }
   cudaStream_t st = (cudaStream_t)stream;
   const Dev d = h->dev();
-  const bool slimwork = policy == SS_V_SLIMWORK;
   const int grid = 8 * h->num_sms;
   const bool prof = h->profiling != 0;
   double iter_ms = 0.0;
   if (prof) SS_CUDA(cudaEventRecord(h->ev_c, st));
 
-  k_init<<<grid, 256, 0, st>>>(d, semiring);
-  k_init_root<<<1, 1, 0, st>>>(d, semiring, root);
+  k_init<<<grid, 256, 0, st>>>(d);
+  k_init_root<<<1, 1, 0, st>>>(d, root);
   SS_CUDA(cudaGetLastError());
 
   const long long max_iter = (long long)h->n + 2;
@@ -557,10 +617,10 @@ ss_status slimsell_bfs(slimsell_handle h, int32_t root, int32_t semiring, int32_
       return SS_ERR_CUDA;
     }
     if (prof) SS_CUDA(cudaEventRecord(h->ev_a, st));
-    ss_status s = launch_iteration(h, d, semiring, slimwork, st);
+    ss_status s = launch_iteration(h, d, semiring, mode, st);
     if (s != SS_OK) return s;
     if (prof) SS_CUDA(cudaEventRecord(h->ev_b, st));
-    k_tail<<<1, 1, 0, st>>>(d, slimwork ? SS_V_SLIMWORK : SS_V_FULL);
+    k_tail<<<1, 1, 0, st>>>(d, policy);
     SS_CUDA(cudaGetLastError());
     SS_CUDA(cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
     SS_CUDA(cudaStreamSynchronize(st));
@@ -573,13 +633,12 @@ ss_status slimsell_bfs(slimsell_handle h, int32_t root, int32_t semiring, int32_
   }
   const int iterations = h->h_ctl->k - 1;
 
-  if (d_parent && semiring != SS_SELMAX) {
-    SS_CUDA(cudaMemsetAsync(h->par, 0xff, sizeof(int) * (size_t)h->n_pad, st));
+  if (d_parent && semiring != SS_SELMAX && h->dp_pass) {
     ss_status s = launch_dp(h, d, st);
     if (s != SS_OK) return s;
   }
   if (d_dist || d_parent) {
-    k_output<<<grid, 256, 0, st>>>(d, d_dist, d_parent, semiring == SS_SELMAX);
+    k_output<<<grid, 256, 0, st>>>(d, d_dist, d_parent);
     SS_CUDA(cudaGetLastError());
   }
   if (prof) SS_CUDA(cudaEventRecord(h->ev_d, st));
@@ -625,6 +684,28 @@ ss_status slimsell_set_profiling(slimsell_handle h, int32_t on) {
   }
   h->profiling = on ? 1 : 0;
   return SS_OK;
+}
+
+ss_status slimsell_set_option(slimsell_handle h, int32_t option, int64_t value) {
+  if (!h) {
+    ss::set_error("slimsell_set_option: NULL handle");
+    return SS_ERR_INVALID;
+  }
+  switch (option) {
+    case SS_OPT_DP_PASS:
+      h->dp_pass = value ? 1 : 0;
+      return SS_OK;
+    case SS_OPT_SMEM_BYTES:
+      if (value < 0 || value > SS_SMEM_MAX_BYTES) {
+        ss::set_error("slimsell_set_option: shared-memory bytes must be in [0, %d]", SS_SMEM_MAX_BYTES);
+        return SS_ERR_INVALID;
+      }
+      h->smem_bytes = (int)value;
+      return SS_OK;
+    default:
+      ss::set_error("slimsell_set_option: unknown option %d", option);
+      return SS_ERR_INVALID;
+  }
 }
 
 }  // extern "C"

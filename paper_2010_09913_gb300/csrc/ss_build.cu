@@ -7,6 +7,7 @@
 //   5. column-major pack: col[cs_i + j*C + l] = invperm[j-th neighbour of row i*C+l,
 //      descending original id], or -1 for padding
 #include <cstdarg>
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -285,7 +286,7 @@ __global__ void k_item_count(const int* cl, int n_c, int W, long long* cnt, long
     }
     int L = cl[i];
     bool split = (W > 0 && L > W);
-    cnt[i] = split ? (L + W - 1) / W : 1;
+    cnt[i] = (L == 0) ? 0 : (split ? (L + W - 1) / W : 1);  // chunks of isolated rows get no item
     if (split_flag) split_flag[i] = split ? 1 : 0;
   }
 }
@@ -301,7 +302,7 @@ __global__ void k_item_fill(const int* cl, int n_c, int W, const long long* off,
       int s = split_idx ? (int)split_idx[i] : -1;
       for (int q = 0; q < cnt; ++q) items[o + q] = make_int4((int)i, q * W, min((q + 1) * W, L), s);
       if (split_n && s >= 0) split_n[s] = cnt;
-    } else {
+    } else if (L > 0) {
       items[o] = make_int4((int)i, 0, L, -1);
     }
   }
@@ -381,6 +382,34 @@ static ss_status make_items(slimsell_graph* h, int W, long long* tmp_cnt, long l
     *split_n_out = split_n;
     *n_split_out = (int)nsplit;
   }
+  return SS_OK;
+}
+
+// Order the BFS work items for the iteration kernels, whose warp w takes items
+// w, w + W, w + 2W, ... (W = warps in the grid): items are sorted by estimated
+// cost (slots plus a fixed per-item overhead), largest first, and every other
+// round of W items is reversed ("snake" order) so each warp's total is balanced.
+static ss_status order_items(slimsell_graph* h, cudaStream_t st) {
+  const int n = h->n_items;
+  if (n <= 1) return SS_OK;
+  std::vector<int4> items((size_t)n), out((size_t)n);
+  SS_CUDA(cudaMemcpyAsync(items.data(), h->items, sizeof(int4) * (size_t)n, cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaStreamSynchronize(st));
+  std::vector<int> idx((size_t)n);
+  for (int i = 0; i < n; ++i) idx[i] = i;
+  const long long C = h->C, overhead = 24LL * h->C;
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
+    return (items[a].z - items[a].y) * C + overhead > (items[b].z - items[b].y) * C + overhead;
+  });
+  const long long W = (long long)h->num_sms * 32;
+  for (long long p = 0; p < n; ++p) {
+    const long long r = p / W, w = p % W;
+    const long long round_len = std::min<long long>(W, n - r * W);
+    const long long src = (r & 1) ? r * W + (round_len - 1 - w) : p;
+    out[(size_t)p] = items[(size_t)idx[(size_t)src]];
+  }
+  SS_CUDA(cudaMemcpyAsync(h->items, out.data(), sizeof(int4) * (size_t)n, cudaMemcpyHostToDevice, st));
+  SS_CUDA(cudaStreamSynchronize(st));
   return SS_OK;
 }
 
@@ -479,6 +508,7 @@ static ss_status build_impl(slimsell_graph* h, const long long* row_ptr, const i
                     nullptr, false, st));
   SS_TRY(make_items(h, h->split_w, tmp_cnt, tmp_flag, tmp_scan, &h->items, &h->n_items, &h->split_n,
                     &h->n_split, true, st));
+  SS_TRY(order_items(h, st));
 
   // 5. pack
   SS_TRY(dmalloc(h, (void**)&h->col, sizeof(int) * (size_t)(slots > 0 ? slots : 1)));
@@ -495,21 +525,24 @@ static ss_status build_impl(slimsell_graph* h, const long long* row_ptr, const i
 static ss_status alloc_state(slimsell_graph* h) {
   ss_status s;
   const size_t np = (size_t)h->n_pad;
+  // bitmap words rounded up to whole int4 groups, plus one spare group
+  h->fb_words = (long long)((((np + 31) / 32) + 3) / 4 * 4 + 4);
   if ((s = dmalloc(h, (void**)&h->lvl, sizeof(int) * np)) != SS_OK) return s;
   if ((s = dmalloc(h, (void**)&h->act, (size_t)h->n_c)) != SS_OK) return s;
-  for (int b = 0; b < 2; ++b) {
-    if ((s = dmalloc(h, (void**)&h->fb[b], np / 8 + 16)) != SS_OK) return s;
-    if ((s = dmalloc(h, (void**)&h->fr[b], sizeof(float) * np)) != SS_OK) return s;
-    if ((s = dmalloc(h, (void**)&h->fx[b], sizeof(int) * np)) != SS_OK) return s;
-  }
+  for (int b = 0; b < 2; ++b)
+    if ((s = dmalloc(h, (void**)&h->fb[b], sizeof(unsigned) * (size_t)h->fb_words)) != SS_OK) return s;
+  if ((s = dmalloc(h, (void**)&h->fr, sizeof(float) * np)) != SS_OK) return s;
   if ((s = dmalloc(h, (void**)&h->par, sizeof(int) * np)) != SS_OK) return s;
   const size_t ns = (size_t)(h->n_split > 0 ? h->n_split : 1);
-  if ((s = dmalloc(h, (void**)&h->xacc, sizeof(unsigned) * ns * h->C)) != SS_OK) return s;
+  if ((s = dmalloc(h, (void**)&h->xacc, sizeof(float) * ns * h->C)) != SS_OK) return s;
+  if ((s = dmalloc(h, (void**)&h->xpar, sizeof(int) * ns * h->C)) != SS_OK) return s;
   if ((s = dmalloc(h, (void**)&h->arrive, sizeof(unsigned) * ns)) != SS_OK) return s;
   if ((s = dmalloc(h, (void**)&h->ctl, sizeof(Ctl))) != SS_OK) return s;
   h->iter_cap = 1 << 16;
   if ((s = dmalloc(h, (void**)&h->iters, sizeof(ss_iter_stats) * (size_t)h->iter_cap)) != SS_OK) return s;
   SS_CUDA(cudaMemset(h->arrive, 0, sizeof(unsigned) * ns));
+  SS_CUDA(cudaMemset(h->fb[0], 0, sizeof(unsigned) * (size_t)h->fb_words));
+  SS_CUDA(cudaMemset(h->fb[1], 0, sizeof(unsigned) * (size_t)h->fb_words));
   SS_CUDA(cudaHostAlloc((void**)&h->h_ctl, sizeof(Ctl), cudaHostAllocDefault));
   SS_CUDA(cudaEventCreate(&h->ev_a));
   SS_CUDA(cudaEventCreate(&h->ev_b));
@@ -521,8 +554,8 @@ static ss_status alloc_state(slimsell_graph* h) {
 void free_handle(slimsell_graph* h) {
   if (!h) return;
   void* ptrs[] = {h->perm, h->invperm, h->rdeg, h->cl, h->cs, h->col, h->items, h->split_n,
-                  h->lvl, h->act, h->fb[0], h->fb[1], h->fr[0], h->fr[1], h->fx[0], h->fx[1],
-                  h->par, h->xacc, h->arrive, h->ctl, h->iters};
+                  h->lvl, h->act, h->fb[0], h->fb[1], h->fr, h->par, h->xacc, h->xpar,
+                  h->arrive, h->ctl, h->iters};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->h_ctl) cudaFreeHost(h->h_ctl);
@@ -540,8 +573,13 @@ ss::Dev slimsell_graph::dev() const {
   d.n = n; d.C = C; d.n_c = n_c; d.n_pad = n_pad; d.n_items = n_items; d.n_split = n_split;
   d.perm = perm; d.invperm = invperm; d.rdeg = rdeg; d.cl = cl; d.cs = cs; d.col = col;
   d.items = items; d.split_n = split_n; d.lvl = lvl; d.act = act;
-  d.fb[0] = fb[0]; d.fb[1] = fb[1]; d.fr[0] = fr[0]; d.fr[1] = fr[1]; d.fx[0] = fx[0]; d.fx[1] = fx[1];
-  d.par = par; d.xacc = xacc; d.arrive = arrive; d.ctl = ctl; d.iters = iters; d.iter_cap = iter_cap;
+  d.fb[0] = fb[0]; d.fb[1] = fb[1]; d.fb_words = fb_words;
+  // staged prefix: whole int4 groups, never past the allocated bitmap
+  long long need = ((((long long)n_pad + 31) / 32) + 3) / 4 * 4;
+  long long cap = (long long)(smem_bytes / 16) * 4;
+  d.smem_words = (int)(need < cap ? need : cap);
+  d.fr = fr; d.par = par; d.xacc = xacc; d.xpar = xpar; d.arrive = arrive;
+  d.ctl = ctl; d.iters = iters; d.iter_cap = iter_cap;
   return d;
 }
 

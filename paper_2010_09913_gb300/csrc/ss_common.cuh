@@ -12,6 +12,7 @@
 #define SS_INF 0x7fffffff          // tropical infinity / "unvisited" level
 #define SS_PAD_LEVEL (-1)          // level of padding rows (never unvisited, never in a frontier)
 #define SS_FULL_MASK 0xffffffffu
+#define SS_SMEM_MAX_BYTES 212992   // frontier-bitmap prefix staged per block (1,703,936 vertices)
 
 namespace ss {
 
@@ -53,11 +54,13 @@ struct Dev {
   const int* split_n;   // [n_split] items per split chunk
   int* lvl;             // [n_pad] level (SS_INF = unvisited); the tropical f vector
   unsigned char* act;   // [n_c] SlimWork state: 1 active, 3/2 inactive with zero writes pending, 0 inactive
-  unsigned* fb[2];      // boolean frontier bitmaps (n_pad bits each), indexed by level parity
-  float* fr[2];         // real-semiring frontier values, by level parity
-  int* fx[2];           // sel-max frontier ids (original id + 1, 0 = not in frontier), by parity
-  int* par;             // [n_pad] parents: sel-max p vector (id + 1) / DP result (original id)
-  unsigned* xacc;       // [n_split * C] SlimChunk partial results (semiring-typed bits)
+  unsigned* fb[2];      // frontier bitmaps (n_pad bits each), indexed by level parity
+  long long fb_words;   // allocated words per bitmap
+  int smem_words;       // bitmap words staged in shared memory per block (multiple of 4)
+  float* fr;            // [n_pad] real-semiring value of a row when it entered the frontier
+  int* par;             // [n_pad] parent original id + 1 (0 = none)
+  float* xacc;          // [n_split * C] SlimChunk partial sums (real semiring)
+  int* xpar;            // [n_split * C] SlimChunk partial parents (original id, -1 = none)
   unsigned* arrive;     // [n_split] SlimChunk arrival counters
   Ctl* ctl;
   ss_iter_stats* iters; // [iter_cap]
@@ -85,11 +88,14 @@ struct slimsell_graph {
   int* lvl = nullptr;
   unsigned char* act = nullptr;
   unsigned* fb[2] = {nullptr, nullptr};
-  float* fr[2] = {nullptr, nullptr};
-  int* fx[2] = {nullptr, nullptr};
+  long long fb_words = 0;
+  float* fr = nullptr;
   int* par = nullptr;
-  unsigned* xacc = nullptr;
+  float* xacc = nullptr;
+  int* xpar = nullptr;
   unsigned* arrive = nullptr;
+  int smem_bytes = SS_SMEM_MAX_BYTES;  // bitmap prefix staged in shared memory
+  int dp_pass = 0;                     // 1: parents by a separate DP pass after the iterations
   ss::Ctl* ctl = nullptr;
   ss::Ctl* h_ctl = nullptr;  // pinned host copy
   ss_iter_stats* iters = nullptr;
