@@ -83,7 +83,7 @@ typedef struct {
   int64_t slots;           /* col slots read by the iteration kernels                 */
   int64_t active_chunks;   /* chunks processed (not skipped)                          */
   int32_t variant;         /* ss_policy value actually executed (0..3)                */
-  int32_t reserved;
+  int32_t kernel_ns;       /* iteration kernel time in ns when profiling is on, else 0 */
 } ss_iter_stats;
 
 /* Summary of the last slimsell_bfs call on a handle. */
@@ -124,8 +124,15 @@ ss_status slimsell_build(const int64_t* d_row_ptr, const int32_t* d_col, int32_t
  *   semiring   ss_semiring.
  *   policy     ss_policy.
  *   d_dist     int32[n] or NULL; d_parent int32[n] or NULL (NULL skips the DP pass).
- * Returns after the BFS has finished on `stream` (the iteration loop reads one
- * counter per iteration).  Errors: SS_ERR_INVALID, SS_ERR_CUDA, SS_ERR_UNSUPPORTED.
+ * By default the iterations run as a device-side loop (a conditional CUDA graph
+ * that stops when an iteration discovers nothing) and the call returns once the
+ * work is queued on `stream`; slimsell_get_run_stats waits for it.  With
+ * profiling on (or SS_OPT_DEVICE_LOOP = 0) the host drives the loop, reading
+ * one counter per iteration, and the call returns after the BFS has finished.
+ * The outputs, and the handle's state, belong to this call until `stream`
+ * reaches its end: do not start another call on the same handle from a
+ * different stream before that.
+ * Errors: SS_ERR_INVALID, SS_ERR_CUDA, SS_ERR_UNSUPPORTED.
  */
 ss_status slimsell_bfs(slimsell_handle h, int32_t root, int32_t semiring, int32_t policy,
                        int32_t* d_dist, int32_t* d_parent, void* stream);
@@ -134,8 +141,9 @@ ss_status slimsell_bfs(slimsell_handle h, int32_t root, int32_t semiring, int32_
 ss_status slimsell_get_info(slimsell_handle h, ss_info* out);
 
 /*
- * Statistics of the last slimsell_bfs on this handle.  h_iters (host, may be
- * NULL) receives up to cap per-iteration records.
+ * Statistics of the last slimsell_bfs on this handle (waits for that call's
+ * work to finish).  h_iters (host, may be NULL) receives up to cap
+ * per-iteration records.
  */
 ss_status slimsell_get_run_stats(slimsell_handle h, ss_run_stats* out, ss_iter_stats* h_iters,
                                  int32_t cap);
@@ -145,8 +153,10 @@ typedef enum {
   SS_OPT_DP_PASS = 1,     /* 1: tropical/real/boolean parents by a separate DP pass after the
                              iterations (Section II-C as written); 0 (default): the same parents
                              computed on the fly inside the iterations                        */
-  SS_OPT_SMEM_BYTES = 2   /* bytes of the frontier bitmap staged in shared memory per block,
+  SS_OPT_SMEM_BYTES = 2,  /* bytes of the frontier bitmap staged in shared memory per block,
                              0 .. 212992 (default 212992); results do not depend on it          */
+  SS_OPT_DEVICE_LOOP = 3  /* 1 (default): iterate on the device in a conditional CUDA graph;
+                             0: the host launches each iteration and reads its counter          */
 } ss_option;
 
 /* Set a handle option (applies to later calls).  Errors: SS_ERR_INVALID. */

@@ -41,7 +41,7 @@ class ss_info(ctypes.Structure):
 class ss_iter_stats(ctypes.Structure):
     _fields_ = [("frontier", ctypes.c_int64), ("frontier_degree", ctypes.c_int64),
                 ("slots", ctypes.c_int64), ("active_chunks", ctypes.c_int64),
-                ("variant", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("variant", ctypes.c_int32), ("kernel_ns", ctypes.c_int32)]
 
 
 class ss_run_stats(ctypes.Structure):
@@ -148,7 +148,7 @@ def slimsell_set_profiling(h: int, on: bool) -> None:
     _check("slimsell_set_profiling", lib().slimsell_set_profiling(h, 1 if on else 0))
 
 
-OPT_DP_PASS, OPT_SMEM_BYTES = 1, 2
+OPT_DP_PASS, OPT_SMEM_BYTES, OPT_DEVICE_LOOP = 1, 2, 3
 
 
 def slimsell_set_option(h: int, option: int, value: int) -> None:

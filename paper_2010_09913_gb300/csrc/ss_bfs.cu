@@ -38,22 +38,36 @@ namespace ss {
 
 constexpr int PULL_THREADS = 1024;  // one block per SM, 32 warps
 constexpr int PULL_STEP = 4;        // int4 col loads in flight per lane (16 slots)
+// Stage the bitmap prefix only when the previous iteration read at least this
+// many slots; below it, reading frontier bits from global memory is cheaper.
+constexpr unsigned long long STAGE_MIN_SLOTS = 2ull << 20;
 
 enum { MODE_FULL = 0, MODE_SLIMWORK = 1, MODE_FILTERED = 3 };
 
 __device__ __forceinline__ int4 ld_stream(const int4* p) { return __ldcs(p); }
+
+// Ask the TMA unit to pull [p, p + bytes) into L2 ahead of the warp's loads
+// (p 16-byte aligned, bytes a positive multiple of 16).
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
+}
+
+constexpr int PREFETCH_BYTES = 4096;  // col bytes prefetched ahead of each warp
 
 __device__ __forceinline__ int4 shfl_int4(int4 v, int src) {
   return make_int4(__shfl_sync(SS_FULL_MASK, v.x, src), __shfl_sync(SS_FULL_MASK, v.y, src),
                    __shfl_sync(SS_FULL_MASK, v.z, src), __shfl_sync(SS_FULL_MASK, v.w, src));
 }
 
-// Frontier bit of relabelled vertex c (c = -1 for padding gives 0).
-__device__ __forceinline__ unsigned frontier_bit(const unsigned* sm, int sbits, const unsigned* gbm,
+// Shared-memory image of the bitmap: SMEM_GUARD zero words, then the staged
+// prefix.  The padding marker c = -1 has c >> 5 = -1 and lands on the last guard
+// word, so it needs no branch; vertices past the prefix read the global bitmap.
+constexpr int SMEM_GUARD = 4;
+
+__device__ __forceinline__ unsigned frontier_bit(const unsigned* smw, int sbits, const unsigned* gbm,
                                                  int c) {
-  unsigned w;
-  if ((unsigned)c < (unsigned)sbits) w = sm[c >> 5];
-  else w = (c >= 0) ? __ldg(gbm + (c >> 5)) : 0u;
+  const int wi = c >> 5;
+  const unsigned w = (c < sbits) ? smw[wi] : __ldg(gbm + wi);
   return (w >> (c & 31)) & 1u;
 }
 
@@ -157,11 +171,53 @@ __device__ __forceinline__ void scan_quad(const Dev& d, const unsigned* sm, int 
   for (int r = 0; r < 4; ++r) hit[r] = frontier_bit(sm, sbits, gbm, cc[r]);
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
-    if (hit[r]) {
-      if (first[r] < 0) first[r] = cc[r];
-      if (SR == SS_REAL) sum[r] += __ldg(d.fr + cc[r]);
-    }
+    first[r] = (hit[r] && first[r] < 0) ? cc[r] : first[r];
+    if (SR == SS_REAL && hit[r]) sum[r] += __ldg(d.fr + cc[r]);
   }
+}
+
+// End of an iteration, run by the last block of the iteration kernel to finish:
+// record statistics, test convergence, advance k and (in the device-side loop)
+// set the loop condition.  The loop also stops, flagging an error, if k passes
+// n + 1 or more than n vertices were counted, which a correct BFS never does,
+// so the device loop always terminates.
+__device__ void iteration_tail(const Dev& d, int variant, cudaGraphConditionalHandle cond,
+                               int use_cond) {
+  Ctl* c = d.ctl;
+  const int k = c->k;
+  const unsigned long long nc = atomicAdd(&c->new_count, 0ull);
+  const unsigned long long nd = atomicAdd(&c->new_deg, 0ull);
+  const unsigned long long sl = atomicAdd(&c->slots, 0ull);
+  const unsigned long long ac = atomicAdd(&c->active, 0ull);
+  if (k < d.iter_cap) {
+    ss_iter_stats s;
+    s.frontier = (long long)nc;
+    s.frontier_degree = (long long)nd;
+    s.slots = (long long)sl;
+    s.active_chunks = (long long)ac;
+    s.variant = variant;
+    s.kernel_ns = 0;
+    d.iters[k] = s;
+  }
+  c->reached += nc;
+  c->reached_deg += nd;
+  c->total_slots += sl;
+  c->prev_slots = sl;
+  c->variant = variant;
+  bool stop = (nc == 0);
+  if (k >= d.n + 1 || c->reached > (unsigned long long)d.n) {
+    c->error |= 1;
+    stop = true;
+  }
+  if (stop) c->done = 1;
+  c->new_count = 0;
+  c->new_deg = 0;
+  c->slots = 0;
+  c->active = 0;
+  c->k = k + 1;
+  c->blocks_done = 0;
+  __threadfence();
+  if (use_cond) cudaGraphSetConditional(cond, stop ? 0u : 1u);
 }
 
 extern __shared__ __align__(16) unsigned ss_smem_bits[];
@@ -171,7 +227,9 @@ extern __shared__ __align__(16) unsigned ss_smem_bits[];
 // the item list is ordered for that assignment); it reads the descriptors and
 // SlimWork states of 32 of them at once (one per lane) and walks the active ones.
 template <int SR, int C, int MODE>
-__global__ void __launch_bounds__(PULL_THREADS, 1) k_pull(Dev d) {
+__global__ void __launch_bounds__(PULL_THREADS, 1) k_pull(Dev d, int variant,
+                                                          cudaGraphConditionalHandle cond,
+                                                          int use_cond) {
   constexpr int Q = C / 4;
   if (d.ctl->done) return;
   const int k = d.ctl->k;
@@ -180,12 +238,19 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_pull(Dev d) {
   const int wid = blockIdx.x * (PULL_THREADS / 32) + (threadIdx.x >> 5);
   const int nw = gridDim.x * (PULL_THREADS / 32);
   const unsigned* gbm = d.fb[km1 & 1];
-  // stage the bitmap prefix of f_{k-1}
-  const int sw = d.smem_words;
-  for (int i = threadIdx.x; i < (sw >> 2); i += PULL_THREADS)
-    reinterpret_cast<int4*>(ss_smem_bits)[i] = __ldg(reinterpret_cast<const int4*>(gbm) + i);
+  // stage the bitmap prefix of f_{k-1} with asynchronous 16-byte copies
+  const int sw = (d.ctl->prev_slots >= STAGE_MIN_SLOTS) ? d.smem_words : 0;
+  {
+    if (threadIdx.x < SMEM_GUARD) ss_smem_bits[threadIdx.x] = 0u;
+    const unsigned sbase = (unsigned)__cvta_generic_to_shared(ss_smem_bits + SMEM_GUARD);
+    for (int i = threadIdx.x; i < (sw >> 2); i += PULL_THREADS)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sbase + 16u * (unsigned)i),
+                   "l"(reinterpret_cast<const int4*>(gbm) + i)
+                   : "memory");
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+  }
   __syncthreads();
-  const unsigned* sm = ss_smem_bits;
+  const unsigned* sm = ss_smem_bits + SMEM_GUARD;
   const int sbits = sw * 32;
   Counters cnt;
   unsigned long long lane_slots = 0;
@@ -215,6 +280,19 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_pull(Dev d) {
       const int4 item = shfl_int4(my_item, src);
       const long long start = __shfl_sync(SS_FULL_MASK, my_start, src);
       const int chunk = item.x;
+      // L2 prefetch: the head of this item beyond the first step, and of the next item
+      if (lane == src) {
+        const unsigned bytes = (unsigned)(item.z - item.y) * C * 4u;
+        if (bytes > 2048u)
+          prefetch_l2(d.col + start + 512, min(bytes - 2048u, (unsigned)PREFETCH_BYTES));
+      }
+      if (todo) {
+        const int nxt = __ffs(todo) - 1;
+        if (lane == nxt) {
+          const unsigned bytes = (unsigned)(my_item.z - my_item.y) * C * 4u;
+          prefetch_l2(d.col + my_start, min(bytes, (unsigned)PREFETCH_BYTES));
+        }
+      }
       // levels of this lane's 4 rows (prefetched; only this chunk's post writes them)
       const int4 lv = *reinterpret_cast<const int4*>(d.lvl + chunk * C + 4 * (lane % Q));
       const int L[4] = {lv.x, lv.y, lv.z, lv.w};
@@ -233,6 +311,14 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_pull(Dev d) {
           if (!__any_sync(SS_FULL_MASK, need)) break;
           if (!need) continue;
         }
+        // keep the prefetch PREFETCH_BYTES ahead inside long items (one lane issues it)
+        if (lane == 0) {
+          const long long ahead = (long long)(q0 + 32 * PULL_STEP) * 16 + PREFETCH_BYTES;
+          const long long total = (long long)nq * 16;
+          if (ahead < total)
+            prefetch_l2(reinterpret_cast<const char*>(base) + ahead,
+                        (unsigned)min(total - ahead, (long long)(32 * PULL_STEP * 16)));
+        }
         int4 c[PULL_STEP];
 #pragma unroll
         for (int u = 0; u < PULL_STEP; ++u) {
@@ -241,7 +327,8 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_pull(Dev d) {
           if (MODE == MODE_FILTERED && q < nq) lane_slots += 4;
         }
 #pragma unroll
-        for (int u = 0; u < PULL_STEP; ++u) scan_quad<SR>(d, sm, sbits, gbm, c[u], first, sum);
+        for (int u = 0; u < PULL_STEP; ++u)
+          if (q0 + 32 * u < nq) scan_quad<SR>(d, sm, sbits, gbm, c[u], first, sum);  // warp-uniform
         if (MODE == MODE_FILTERED) {  // a row is done once visited or (not real) hit
           need = false;
 #pragma unroll
@@ -257,13 +344,19 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_pull(Dev d) {
         acc.best[r] = (first[r] >= 0 && L[r] == SS_INF) ? __ldg(d.perm + first[r]) : -1;
         acc.sum[r] = sum[r];
       }
+      const bool any_hit = (acc.best[0] >= 0) | (acc.best[1] >= 0) | (acc.best[2] >= 0) |
+                           (acc.best[3] >= 0) |
+                           (SR == SS_REAL && ((sum[0] != 0.f) | (sum[1] != 0.f) | (sum[2] != 0.f) |
+                                              (sum[3] != 0.f)));
+      if (__any_sync(SS_FULL_MASK, any_hit)) {  // lanes with equal lane mod Q share rows
 #pragma unroll
-      for (int off = Q; off < 32; off <<= 1)
+        for (int off = Q; off < 32; off <<= 1)
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          acc.best[r] = max(acc.best[r], __shfl_xor_sync(SS_FULL_MASK, acc.best[r], off));
-          if (SR == SS_REAL) acc.sum[r] += __shfl_xor_sync(SS_FULL_MASK, acc.sum[r], off);
-        }
+          for (int r = 0; r < 4; ++r) {
+            acc.best[r] = max(acc.best[r], __shfl_xor_sync(SS_FULL_MASK, acc.best[r], off));
+            if (SR == SS_REAL) acc.sum[r] += __shfl_xor_sync(SS_FULL_MASK, acc.sum[r], off);
+          }
+      }
       if (item.w >= 0) {  // SlimChunk: combine partial rows, the last arriving item post-processes
         const size_t xo = (size_t)item.w * C + 4 * lane;
         if (lane < Q) {
@@ -322,34 +415,16 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_pull(Dev d) {
                                                  : &d.ctl->active;
       atomicAdd(dst, s);
     }
+    __threadfence();
   }
-}
-
-// End of an iteration: record statistics, test convergence, advance k.
-__global__ void k_tail(Dev d, int variant) {
-  Ctl* c = d.ctl;
-  if (c->done) return;
-  const int k = c->k;
-  if (k < d.iter_cap) {
-    ss_iter_stats s;
-    s.frontier = (long long)c->new_count;
-    s.frontier_degree = (long long)c->new_deg;
-    s.slots = (long long)c->slots;
-    s.active_chunks = (long long)c->active;
-    s.variant = variant;
-    s.reserved = 0;
-    d.iters[k] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned prev = atomicAdd(&d.ctl->blocks_done, 1u);
+    if (prev == gridDim.x - 1) {
+      __threadfence();
+      iteration_tail(d, variant, cond, use_cond);
+    }
   }
-  c->reached += c->new_count;
-  c->reached_deg += c->new_deg;
-  c->total_slots += c->slots;
-  c->variant = variant;
-  if (c->new_count == 0) c->done = 1;
-  c->new_count = 0;
-  c->new_deg = 0;
-  c->slots = 0;
-  c->active = 0;
-  c->k = k + 1;
 }
 
 __global__ void k_init(Dev d) {
@@ -377,10 +452,10 @@ __global__ void k_init_root(Dev d, int root) {
   c->k = 1; c->done = 0; c->error = 0; c->variant = -1;
   c->new_count = 0; c->new_deg = 0; c->slots = 0; c->active = 0;
   c->reached = 1; c->reached_deg = (unsigned long long)d.rdeg[r];
-  c->total_slots = 0; c->dp_slots = 0;
+  c->total_slots = 0; c->dp_slots = 0; c->blocks_done = 0; c->prev_slots = ~0ull;
   ss_iter_stats s;
   s.frontier = 1; s.frontier_degree = d.rdeg[r]; s.slots = 0; s.active_chunks = 0;
-  s.variant = -1; s.reserved = 0;
+  s.variant = -1; s.kernel_ns = 0;
   d.iters[0] = s;
 }
 
@@ -507,46 +582,119 @@ __global__ void k_output(Dev d, int* dist, int* parent) {
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
+struct IterLaunch {
+  int variant;
+  cudaGraphConditionalHandle cond;
+  int use_cond;
+};
+
 template <int SR, int C, int MODE>
-static ss_status launch_pull(const slimsell_graph* h, const Dev& d, cudaStream_t st) {
+static ss_status launch_pull(const slimsell_graph* h, const Dev& d, const IterLaunch& il,
+                             cudaStream_t st) {
   static bool configured = false;
   if (!configured) {
     SS_CUDA(cudaFuncSetAttribute(k_pull<SR, C, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 SS_SMEM_MAX_BYTES));
+                                 SS_SMEM_LIMIT_BYTES));
     configured = true;
   }
-  k_pull<SR, C, MODE><<<h->num_sms, PULL_THREADS, (size_t)d.smem_words * 4, st>>>(d);
+  k_pull<SR, C, MODE><<<h->num_sms, PULL_THREADS, (size_t)(d.smem_words + SMEM_GUARD) * 4, st>>>(
+      d, il.variant, il.cond, il.use_cond);
   SS_CUDA(cudaGetLastError());
   return SS_OK;
 }
 
 template <int SR, int MODE>
-static ss_status launch_pull_c(const slimsell_graph* h, const Dev& d, cudaStream_t st) {
+static ss_status launch_pull_c(const slimsell_graph* h, const Dev& d, const IterLaunch& il,
+                               cudaStream_t st) {
   switch (h->C) {
-    case 8: return launch_pull<SR, 8, MODE>(h, d, st);
-    case 16: return launch_pull<SR, 16, MODE>(h, d, st);
-    case 32: return launch_pull<SR, 32, MODE>(h, d, st);
-    default: return launch_pull<SR, 64, MODE>(h, d, st);
+    case 8: return launch_pull<SR, 8, MODE>(h, d, il, st);
+    case 16: return launch_pull<SR, 16, MODE>(h, d, il, st);
+    case 32: return launch_pull<SR, 32, MODE>(h, d, il, st);
+    default: return launch_pull<SR, 64, MODE>(h, d, il, st);
   }
 }
 
 template <int SR>
-static ss_status launch_pull_m(const slimsell_graph* h, const Dev& d, int mode, cudaStream_t st) {
+static ss_status launch_pull_m(const slimsell_graph* h, const Dev& d, int mode, const IterLaunch& il,
+                               cudaStream_t st) {
   switch (mode) {
-    case MODE_FULL: return launch_pull_c<SR, MODE_FULL>(h, d, st);
-    case MODE_SLIMWORK: return launch_pull_c<SR, MODE_SLIMWORK>(h, d, st);
-    default: return launch_pull_c<SR, MODE_FILTERED>(h, d, st);
+    case MODE_FULL: return launch_pull_c<SR, MODE_FULL>(h, d, il, st);
+    case MODE_SLIMWORK: return launch_pull_c<SR, MODE_SLIMWORK>(h, d, il, st);
+    default: return launch_pull_c<SR, MODE_FILTERED>(h, d, il, st);
   }
 }
 
 static ss_status launch_iteration(const slimsell_graph* h, const Dev& d, int sr, int mode,
-                                  cudaStream_t st) {
+                                  const IterLaunch& il, cudaStream_t st) {
   switch (sr) {
-    case SS_TROPICAL: return launch_pull_m<SS_TROPICAL>(h, d, mode, st);
-    case SS_REAL: return launch_pull_m<SS_REAL>(h, d, mode, st);
-    case SS_BOOLEAN: return launch_pull_m<SS_BOOLEAN>(h, d, mode, st);
-    default: return launch_pull_m<SS_SELMAX>(h, d, mode, st);
+    case SS_TROPICAL: return launch_pull_m<SS_TROPICAL>(h, d, mode, il, st);
+    case SS_REAL: return launch_pull_m<SS_REAL>(h, d, mode, il, st);
+    case SS_BOOLEAN: return launch_pull_m<SS_BOOLEAN>(h, d, mode, il, st);
+    default: return launch_pull_m<SS_SELMAX>(h, d, mode, il, st);
   }
+}
+
+// Device-side iteration loop: a graph holding one conditional WHILE node whose
+// body is the iteration kernel; the kernel's last block sets the condition.
+// Built once per (semiring, mode, staged-prefix size) and cached in the handle.
+static ss_status loop_graph(slimsell_graph* h, const Dev& d, int sr, int mode, int variant,
+                            cudaGraphExec_t* out) {
+  cudaGraphExec_t& slot = h->loop_exec[sr][mode];
+  if (slot && h->loop_smem_words[sr][mode] == d.smem_words) {
+    *out = slot;
+    return SS_OK;
+  }
+  if (slot) {
+    SS_CUDA(cudaGraphExecDestroy(slot));
+    slot = nullptr;
+  }
+  cudaGraph_t g = nullptr;
+  SS_CUDA(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle cond;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_fail(e, "cudaGraphConditionalHandleCreate");
+  }
+  cudaGraphNodeParams p = {};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = cond;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &p);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_fail(e, "cudaGraphAddNode(conditional)");
+  }
+  cudaGraph_t body = p.conditional.phGraph_out[0];
+  cudaStream_t cs = nullptr;
+  e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
+                                                          cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) {
+    if (cs) cudaStreamDestroy(cs);
+    cudaGraphDestroy(g);
+    return cuda_fail(e, "cudaStreamBeginCaptureToGraph");
+  }
+  IterLaunch il{variant, cond, 1};
+  ss_status s = launch_iteration(h, d, sr, mode, il, cs);
+  cudaGraph_t captured = nullptr;
+  e = cudaStreamEndCapture(cs, &captured);
+  cudaStreamDestroy(cs);
+  if (s != SS_OK || e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return s != SS_OK ? s : cuda_fail(e, "cudaStreamEndCapture");
+  }
+  e = cudaGraphInstantiate(&slot, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    slot = nullptr;
+    return cuda_fail(e, "cudaGraphInstantiate");
+  }
+  h->loop_smem_words[sr][mode] = d.smem_words;
+  *out = slot;
+  return SS_OK;
 }
 
 template <int C>
@@ -567,6 +715,31 @@ static ss_status launch_dp(const slimsell_graph* h, const Dev& d, cudaStream_t s
   }
 }
 
+}  // namespace ss
+
+namespace ss {
+// Read back the counters of the last call once its work has finished.
+static ss_status finish_run(slimsell_graph* h) {
+  if (!h->pending) return SS_OK;
+  SS_CUDA(cudaEventSynchronize(h->ev_done));
+  h->pending = 0;
+  const Ctl& c = *h->h_ctl;
+  h->last.iterations = c.k - 1;
+  h->last.reached = (long long)c.reached;
+  h->last.reached_degree = (long long)c.reached_deg;
+  h->last.slots = (long long)c.total_slots;
+  h->last.dp_slots = (long long)c.dp_slots;
+  if (h->profiling) {
+    float ms = 0.f;
+    SS_CUDA(cudaEventElapsedTime(&ms, h->ev_c, h->ev_d));
+    h->last.total_ms = ms;
+  }
+  if (c.error) {
+    set_error("slimsell_bfs: iteration limit reached (device error flags %d)", c.error);
+    return SS_ERR_CUDA;
+  }
+  return SS_OK;
+}
 }  // namespace ss
 
 extern "C" {
@@ -603,6 +776,10 @@ ss_status slimsell_bfs(slimsell_handle h, int32_t root, int32_t semiring, int32_
   const Dev d = h->dev();
   const int grid = 8 * h->num_sms;
   const bool prof = h->profiling != 0;
+  const bool device_loop = h->device_loop && !prof;
+  if (h->pending) SS_CUDA(cudaEventSynchronize(h->ev_done));  // statistics of the previous call
+  h->pending = 0;
+  h->iter_ns.clear();
   double iter_ms = 0.0;
   if (prof) SS_CUDA(cudaEventRecord(h->ev_c, st));
 
@@ -610,28 +787,34 @@ ss_status slimsell_bfs(slimsell_handle h, int32_t root, int32_t semiring, int32_
   k_init_root<<<1, 1, 0, st>>>(d, root);
   SS_CUDA(cudaGetLastError());
 
-  const long long max_iter = (long long)h->n + 2;
-  for (long long it = 0;; ++it) {
-    if (it > max_iter) {
-      set_error("slimsell_bfs: no convergence after %lld iterations", it);
-      return SS_ERR_CUDA;
-    }
-    if (prof) SS_CUDA(cudaEventRecord(h->ev_a, st));
-    ss_status s = launch_iteration(h, d, semiring, mode, st);
+  if (device_loop) {
+    cudaGraphExec_t exec = nullptr;
+    ss_status s = loop_graph(h, d, semiring, mode, policy, &exec);
     if (s != SS_OK) return s;
-    if (prof) SS_CUDA(cudaEventRecord(h->ev_b, st));
-    k_tail<<<1, 1, 0, st>>>(d, policy);
-    SS_CUDA(cudaGetLastError());
-    SS_CUDA(cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
-    SS_CUDA(cudaStreamSynchronize(st));
-    if (prof) {
-      float ms = 0.f;
-      SS_CUDA(cudaEventElapsedTime(&ms, h->ev_a, h->ev_b));
-      iter_ms += ms;
+    SS_CUDA(cudaGraphLaunch(exec, st));
+  } else {
+    const IterLaunch il{policy, 0, 0};
+    const long long max_iter = (long long)h->n + 2;
+    for (long long it = 0;; ++it) {
+      if (it > max_iter) {
+        set_error("slimsell_bfs: no convergence after %lld iterations", it);
+        return SS_ERR_CUDA;
+      }
+      if (prof) SS_CUDA(cudaEventRecord(h->ev_a, st));
+      ss_status s = launch_iteration(h, d, semiring, mode, il, st);
+      if (s != SS_OK) return s;
+      if (prof) SS_CUDA(cudaEventRecord(h->ev_b, st));
+      SS_CUDA(cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+      SS_CUDA(cudaStreamSynchronize(st));
+      if (prof) {
+        float ms = 0.f;
+        SS_CUDA(cudaEventElapsedTime(&ms, h->ev_a, h->ev_b));
+        iter_ms += ms;
+        h->iter_ns.push_back((int)(ms * 1.0e6f));
+      }
+      if (h->h_ctl->done) break;
     }
-    if (h->h_ctl->done) break;
   }
-  const int iterations = h->h_ctl->k - 1;
 
   if (d_parent && semiring != SS_SELMAX && h->dp_pass) {
     ss_status s = launch_dp(h, d, st);
@@ -643,21 +826,12 @@ ss_status slimsell_bfs(slimsell_handle h, int32_t root, int32_t semiring, int32_
   }
   if (prof) SS_CUDA(cudaEventRecord(h->ev_d, st));
   SS_CUDA(cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
-  SS_CUDA(cudaStreamSynchronize(st));
-  const Ctl& c = *h->h_ctl;
-  h->last.iterations = iterations;
+  SS_CUDA(cudaEventRecord(h->ev_done, st));
   h->last.semiring = semiring;
-  h->last.reached = (long long)c.reached;
-  h->last.reached_degree = (long long)c.reached_deg;
-  h->last.slots = (long long)c.total_slots;
-  h->last.dp_slots = (long long)c.dp_slots;
   h->last.iter_kernel_ms = iter_ms;
   h->last.total_ms = 0.0;
-  if (prof) {
-    float ms = 0.f;
-    SS_CUDA(cudaEventElapsedTime(&ms, h->ev_c, h->ev_d));
-    h->last.total_ms = ms;
-  }
+  h->pending = 1;
+  if (!device_loop) return finish_run(h);
   return SS_OK;
 }
 
@@ -667,14 +841,17 @@ ss_status slimsell_get_run_stats(slimsell_handle h, ss_run_stats* out, ss_iter_s
     ss::set_error("slimsell_get_run_stats: NULL argument");
     return SS_ERR_INVALID;
   }
+  ss_status s = ss::finish_run(h);
   *out = h->last;
   if (h_iters && cap > 0) {
     int cnt = h->last.iterations + 1;
     if (cnt > cap) cnt = cap;
     if (cnt > h->iter_cap) cnt = h->iter_cap;
     SS_CUDA(cudaMemcpy(h_iters, h->iters, sizeof(ss_iter_stats) * (size_t)cnt, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < cnt; ++i)
+      h_iters[i].kernel_ns = (i >= 1 && i - 1 < (int)h->iter_ns.size()) ? h->iter_ns[i - 1] : 0;
   }
-  return SS_OK;
+  return s;
 }
 
 ss_status slimsell_set_profiling(slimsell_handle h, int32_t on) {
@@ -694,6 +871,9 @@ ss_status slimsell_set_option(slimsell_handle h, int32_t option, int64_t value) 
   switch (option) {
     case SS_OPT_DP_PASS:
       h->dp_pass = value ? 1 : 0;
+      return SS_OK;
+    case SS_OPT_DEVICE_LOOP:
+      h->device_loop = value ? 1 : 0;
       return SS_OK;
     case SS_OPT_SMEM_BYTES:
       if (value < 0 || value > SS_SMEM_MAX_BYTES) {

@@ -548,6 +548,8 @@ static ss_status alloc_state(slimsell_graph* h) {
   SS_CUDA(cudaEventCreate(&h->ev_b));
   SS_CUDA(cudaEventCreate(&h->ev_c));
   SS_CUDA(cudaEventCreate(&h->ev_d));
+  SS_CUDA(cudaEventCreateWithFlags(&h->ev_done, cudaEventDisableTiming));
+  SS_CUDA(cudaMemset(h->ctl, 0, sizeof(Ctl)));
   return SS_OK;
 }
 
@@ -563,6 +565,13 @@ void free_handle(slimsell_graph* h) {
   if (h->ev_b) cudaEventDestroy(h->ev_b);
   if (h->ev_c) cudaEventDestroy(h->ev_c);
   if (h->ev_d) cudaEventDestroy(h->ev_d);
+  if (h->ev_done) {
+    cudaEventSynchronize(h->ev_done);
+    cudaEventDestroy(h->ev_done);
+  }
+  for (auto& row : h->loop_exec)
+    for (auto& e : row)
+      if (e) cudaGraphExecDestroy(e);
   delete h;
 }
 

@@ -6,6 +6,7 @@
 
 #include <cstdio>
 #include <string>
+#include <vector>
 
 #include "slimsell.h"
 
@@ -13,6 +14,7 @@
 #define SS_PAD_LEVEL (-1)          // level of padding rows (never unvisited, never in a frontier)
 #define SS_FULL_MASK 0xffffffffu
 #define SS_SMEM_MAX_BYTES 212992   // frontier-bitmap prefix staged per block (1,703,936 vertices)
+#define SS_SMEM_LIMIT_BYTES 214016 // dynamic shared memory requested at most (prefix + guard)
 
 namespace ss {
 
@@ -39,6 +41,9 @@ struct Ctl {
   unsigned long long reached_deg; // cumulative degree sum
   unsigned long long total_slots; // cumulative slots
   unsigned long long dp_slots;    // slots read by the DP pass
+  unsigned int blocks_done;       // blocks of the current iteration kernel that finished
+  unsigned int pad0;
+  unsigned long long prev_slots;  // slots read by the previous iteration (staging decision)
 };
 
 // Flat view of the handle's device buffers handed to kernels by value.
@@ -105,6 +110,12 @@ struct slimsell_graph {
   ss_run_stats last{};
   int profiling = 0;
   cudaEvent_t ev_a = nullptr, ev_b = nullptr, ev_c = nullptr, ev_d = nullptr;
+  cudaEvent_t ev_done = nullptr;       // end of the last call's work on its stream
+  int pending = 0;                     // last-run statistics not yet read back
+  int device_loop = 1;                 // iterate with a conditional CUDA graph
+  cudaGraphExec_t loop_exec[4][4] = {};  // [semiring][mode] device-side iteration loops
+  int loop_smem_words[4][4] = {};
+  std::vector<int> iter_ns;            // per-iteration kernel time of the last profiled call
 
   ss::Dev dev() const;
 };

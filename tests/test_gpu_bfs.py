@@ -125,6 +125,27 @@ def test_options_do_not_change_results(smem, dp_pass):
     G.close()
 
 
+def test_device_loop_matches_host_loop():
+    """The conditional-graph iteration loop and the host-driven loop agree exactly."""
+    g = gg.kronecker(12, seed=4)
+    G = ss.SlimSellGraph.from_host(g.row_ptr, g.col, C=32, sigma=g.n, split_w=32)
+    for r in gg.roots(g, 3, seed=7):
+        d, p = expected(g, r)
+        for sr in SEMIRINGS:
+            for pol in ("full", "slimwork", "pull_filtered"):
+                res = []
+                for loop in (1, 0):
+                    G.set_option(ss.OPT_DEVICE_LOOP, loop)
+                    dist, parent = run(G, r, sr, pol)
+                    np.testing.assert_array_equal(dist, d)
+                    np.testing.assert_array_equal(parent, p)
+                    st, iters = G.run_stats(cap=64)
+                    res.append((st.iterations, st.reached, st.slots,
+                                [(iters[i].frontier, iters[i].slots) for i in range(st.iterations + 1)]))
+                assert res[0] == res[1]
+    G.close()
+
+
 def test_edge_cases():
     cases = [
         gg.from_edges(1, []),                                      # single vertex, no edges
