@@ -192,5 +192,16 @@ def roots(g: Graph, k: int, seed: int, distinct: bool = True) -> np.ndarray:
     return np.asarray(out, dtype=np.int32)
 
 
+def mlp_weights(seed: int, scale: float = 0.3) -> np.ndarray:
+    """Seeded fp32 parameters for the 16-64-64-4 selector MLP (5508 values, in the
+    order W1[16][64], b1, W2[64][64], b2, W3[64][4], b3); He-style normal weights
+    times `scale`, biases drawn small."""
+    rng = np.random.default_rng(seed)
+    parts = [rng.normal(0, scale * np.sqrt(2.0 / 16), (16, 64)), rng.normal(0, 0.05, 64),
+             rng.normal(0, scale * np.sqrt(2.0 / 64), (64, 64)), rng.normal(0, 0.05, 64),
+             rng.normal(0, scale * np.sqrt(2.0 / 64), (64, 4)), rng.normal(0, 0.05, 4)]
+    return np.concatenate([p.ravel() for p in parts]).astype(np.float32)
+
+
 def num_threads() -> int:
     return int(_load().gg_num_threads())

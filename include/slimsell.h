@@ -57,7 +57,8 @@ typedef enum {
 typedef enum {
   SS_V_FULL = 0,          /* every chunk, every column (plain BFS-SpMV, Section III-A)        */
   SS_V_SLIMWORK = 1,      /* skip chunks whose rows are all visited (SlimWork, Section III-C) */
-  SS_V_PUSH = 2,          /* compacted-frontier push (work-avoidance variant, Section V)      */
+  SS_V_PUSH = 2,          /* compacted-frontier push (work-avoidance variant, Section V); falls
+                             back to PULL_FILTERED when the frontier exceeds the unit buffer  */
   SS_V_PULL_FILTERED = 3, /* pull over unvisited rows only, stopping at the first hit         */
   SS_V_HEURISTIC = 4,     /* per-iteration choice by a frontier-size rule                      */
   SS_V_LEARNED = 5        /* per-iteration choice by the loaded selector MLP                   */
@@ -82,7 +83,7 @@ typedef struct {
   int64_t frontier_degree; /* sum of their degrees                                    */
   int64_t slots;           /* col slots read by the iteration kernels                 */
   int64_t active_chunks;   /* chunks processed (not skipped)                          */
-  int32_t variant;         /* ss_policy value actually executed (0..3)                */
+  int32_t variant;         /* variant actually executed (0 FULL, 1 SLIMWORK, 2 PUSH, 3 FILTERED) */
   int32_t kernel_ns;       /* iteration kernel time in ns when profiling is on, else 0 */
 } ss_iter_stats;
 
@@ -203,6 +204,45 @@ ss_status slimsell_export_layout(slimsell_handle h, int32_t* d_perm, int32_t* d_
  */
 ss_status slimsell_sigma_sort_noalloc(const int64_t* d_row_ptr, int32_t n, int32_t sigma,
                                       int32_t* d_perm, void* stream);
+
+/*
+ * Variant selector (an extension beyond the paper).  The learned policy feeds
+ * 16 features of each iteration to a 16-64-64-4 ReLU MLP whose outputs predict
+ * the log-time of the four variants (FULL, SLIMWORK, PUSH, PULL_FILTERED, in
+ * ss_policy order) and runs the argmin.  Parameters are fp32, inputs first:
+ * W1[16][64], b1[64], W2[64][64], b2[64], W3[64][4], b3[4] (5508 values),
+ * h1 = relu(x W1 + b1), h2 = relu(h1 W2 + b2), y = h2 W3 + b3.
+ */
+#define SS_SELECTOR_FEATURES 16
+#define SS_SELECTOR_HIDDEN 64
+#define SS_SELECTOR_OUTPUTS 4
+#define SS_SELECTOR_PARAMS 5508
+
+/* Copy selector weights (host, len = SS_SELECTOR_PARAMS) to the handle's device
+ * memory; h_weights = NULL unloads them (the learned policy then uses the
+ * heuristic).  Errors: SS_ERR_INVALID, SS_ERR_OOM, SS_ERR_CUDA. */
+ss_status slimsell_selector_load(slimsell_handle h, const float* h_weights, int64_t len);
+
+/* Features of each iteration of the last slimsell_bfs (host, row-major
+ * [min(cap, iterations + 1)][16]; row k = features seen before iteration k). */
+ss_status slimsell_get_features(slimsell_handle h, float* h_out, int32_t cap);
+
+/* Batched MLP forward: d_y[batch][4] = MLP(d_w; d_x[batch][16]) (device, fp32). */
+ss_status slimsell_mlp_forward(const float* d_w, const float* d_x, int32_t batch, float* d_y,
+                               void* stream);
+
+/*
+ * One training step on a minibatch (1 <= batch <= 128): forward, loss =
+ * sum(mask * (y - t)^2) / max(sum(mask), 1) over d_t, d_mask [batch][4],
+ * backward, and (lr > 0) an Adam update (beta1 0.9, beta2 0.999, eps 1e-8,
+ * bias-corrected with `step` >= 1) of d_w using the moment buffers d_adam_m,
+ * d_adam_v [5508].  d_grad [5508] (may be NULL) receives the gradient and
+ * d_loss [1] (may be NULL) the loss, both before the update.  All device.
+ */
+ss_status slimsell_mlp_train_step(float* d_w, float* d_adam_m, float* d_adam_v, int32_t step,
+                                  const float* d_x, const float* d_t, const float* d_mask,
+                                  int32_t batch, float lr, float* d_grad, float* d_loss,
+                                  void* stream);
 
 /* Free the handle and its device buffers (NULL is ignored). */
 void slimsell_destroy(slimsell_handle h);

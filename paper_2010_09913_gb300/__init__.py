@@ -75,6 +75,11 @@ def lib():
         "slimsell_export_layout": (i32, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
         "slimsell_destroy": (None, [_VP]),
         "slimsell_sigma_sort_noalloc": (i32, [_VP, i32, i32, _VP, _VP]),
+        "slimsell_selector_load": (i32, [_VP, _VP, i64]),
+        "slimsell_get_features": (i32, [_VP, _VP, i32]),
+        "slimsell_mlp_forward": (i32, [_VP, _VP, i32, _VP, _VP]),
+        "slimsell_mlp_train_step": (i32, [_VP, _VP, _VP, i32, _VP, _VP, _VP, i32, ctypes.c_float,
+                                          _VP, _VP, _VP]),
         "slimsell_last_error": (ctypes.c_char_p, []),
         "slimsell_version": (ctypes.c_char_p, []),
     }
@@ -90,7 +95,8 @@ def exported_symbols() -> list[str]:
     return ["slimsell_build", "slimsell_bfs", "slimsell_get_info", "slimsell_get_run_stats",
             "slimsell_set_profiling", "slimsell_set_option", "slimsell_export_layout",
             "slimsell_destroy",
-            "slimsell_sigma_sort_noalloc",
+            "slimsell_sigma_sort_noalloc", "slimsell_selector_load", "slimsell_get_features",
+            "slimsell_mlp_forward", "slimsell_mlp_train_step",
             "slimsell_last_error", "slimsell_version"]
 
 
@@ -167,6 +173,43 @@ def slimsell_sigma_sort_noalloc(row_ptr: torch.Tensor, n: int, sigma: int, perm:
     _check("slimsell_sigma_sort_noalloc", lib().slimsell_sigma_sort_noalloc(
         _ptr(row_ptr, torch.int64, "row_ptr"), int(n), int(sigma), _ptr(perm, torch.int32, "perm"),
         _stream(stream)))
+
+
+N_FEATURES, N_OUTPUTS, N_PARAMS = 16, 4, 5508
+
+
+def slimsell_selector_load(h: int, weights) -> None:
+    """weights: 5508 float32 values (numpy array or CPU tensor), or None to unload."""
+    if weights is None:
+        _check("slimsell_selector_load", lib().slimsell_selector_load(h, None, 0))
+        return
+    import numpy as np
+    w = np.ascontiguousarray(np.asarray(weights, dtype=np.float32))
+    _check("slimsell_selector_load", lib().slimsell_selector_load(
+        h, w.ctypes.data_as(ctypes.c_void_p), int(w.size)))
+
+
+def slimsell_get_features(h: int, cap: int):
+    import numpy as np
+    out = np.zeros((cap, N_FEATURES), dtype=np.float32)
+    _check("slimsell_get_features", lib().slimsell_get_features(
+        h, out.ctypes.data_as(ctypes.c_void_p), int(cap)))
+    return out
+
+
+def slimsell_mlp_forward(w: torch.Tensor, x: torch.Tensor, y: torch.Tensor, stream=None) -> None:
+    _check("slimsell_mlp_forward", lib().slimsell_mlp_forward(
+        _ptr(w, torch.float32, "w"), _ptr(x, torch.float32, "x"), int(x.shape[0]),
+        _ptr(y, torch.float32, "y"), _stream(stream)))
+
+
+def slimsell_mlp_train_step(w, m, v, step, x, t, mask, lr, grad=None, loss=None, stream=None) -> None:
+    _check("slimsell_mlp_train_step", lib().slimsell_mlp_train_step(
+        _ptr(w, torch.float32, "w"), _ptr(m, torch.float32, "m") if m is not None else None,
+        _ptr(v, torch.float32, "v") if v is not None else None, int(step),
+        _ptr(x, torch.float32, "x"), _ptr(t, torch.float32, "t"), _ptr(mask, torch.float32, "mask"),
+        int(x.shape[0]), float(lr), _ptr(grad, torch.float32, "grad") if grad is not None else None,
+        _ptr(loss, torch.float32, "loss") if loss is not None else None, _stream(stream)))
 
 
 def slimsell_destroy(h: int) -> None:

@@ -32,7 +32,7 @@
 // lane l always meets rows 4*(l mod C/4) .. +3; lanes sharing rows are combined
 // with xor-shuffles.  Split chunks (SlimChunk) combine partial rows with
 // atomics; the last item of a chunk to arrive runs the post-processing.
-#include "ss_common.cuh"
+#include "ss_device.cuh"
 
 namespace ss {
 
@@ -95,6 +95,7 @@ __device__ __forceinline__ void gather_bits(unsigned nib, int lane, unsigned* lo
 
 struct Counters {
   unsigned long long nw = 0, deg = 0, slots = 0, act = 0;
+  unsigned maxdeg = 0;
 };
 
 // Per-row result of one item: best = largest original id among frontier
@@ -135,7 +136,10 @@ __device__ __forceinline__ void post_chunk(const Dev& d, int k, int chunk, int l
       const int D[4] = {dg.x, dg.y, dg.z, dg.w};
 #pragma unroll
       for (int r = 0; r < 4; ++r)
-        if (nib >> r & 1u) cnt.deg += (unsigned long long)D[r];
+        if (nib >> r & 1u) {
+          cnt.deg += (unsigned long long)D[r];
+          cnt.maxdeg = max(cnt.maxdeg, (unsigned)D[r]);
+        }
       cnt.nw += __popc(nib);
     }
   }
@@ -176,50 +180,6 @@ __device__ __forceinline__ void scan_quad(const Dev& d, const unsigned* sm, int 
   }
 }
 
-// End of an iteration, run by the last block of the iteration kernel to finish:
-// record statistics, test convergence, advance k and (in the device-side loop)
-// set the loop condition.  The loop also stops, flagging an error, if k passes
-// n + 1 or more than n vertices were counted, which a correct BFS never does,
-// so the device loop always terminates.
-__device__ void iteration_tail(const Dev& d, int variant, cudaGraphConditionalHandle cond,
-                               int use_cond) {
-  Ctl* c = d.ctl;
-  const int k = c->k;
-  const unsigned long long nc = atomicAdd(&c->new_count, 0ull);
-  const unsigned long long nd = atomicAdd(&c->new_deg, 0ull);
-  const unsigned long long sl = atomicAdd(&c->slots, 0ull);
-  const unsigned long long ac = atomicAdd(&c->active, 0ull);
-  if (k < d.iter_cap) {
-    ss_iter_stats s;
-    s.frontier = (long long)nc;
-    s.frontier_degree = (long long)nd;
-    s.slots = (long long)sl;
-    s.active_chunks = (long long)ac;
-    s.variant = variant;
-    s.kernel_ns = 0;
-    d.iters[k] = s;
-  }
-  c->reached += nc;
-  c->reached_deg += nd;
-  c->total_slots += sl;
-  c->prev_slots = sl;
-  c->variant = variant;
-  bool stop = (nc == 0);
-  if (k >= d.n + 1 || c->reached > (unsigned long long)d.n) {
-    c->error |= 1;
-    stop = true;
-  }
-  if (stop) c->done = 1;
-  c->new_count = 0;
-  c->new_deg = 0;
-  c->slots = 0;
-  c->active = 0;
-  c->k = k + 1;
-  c->blocks_done = 0;
-  __threadfence();
-  if (use_cond) cudaGraphSetConditional(cond, stop ? 0u : 1u);
-}
-
 extern __shared__ __align__(16) unsigned ss_smem_bits[];
 
 // One frontier expansion x_k = A (x)_S f_{k-1} with fused post-processing.
@@ -239,7 +199,10 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_pull(Dev d, int variant,
   const int nw = gridDim.x * (PULL_THREADS / 32);
   const unsigned* gbm = d.fb[km1 & 1];
   // stage the bitmap prefix of f_{k-1} with asynchronous 16-byte copies
-  const int sw = (d.ctl->prev_slots >= STAGE_MIN_SLOTS) ? d.smem_words : 0;
+  const int pv = d.ctl->prev_variant;
+  const bool light = (pv == VAR_FULL || pv == VAR_SLIMWORK || pv == VAR_FILTERED) &&
+                     d.ctl->prev_slots < STAGE_MIN_SLOTS;
+  const int sw = light ? 0 : d.smem_words;
   {
     if (threadIdx.x < SMEM_GUARD) ss_smem_bits[threadIdx.x] = 0u;
     const unsigned sbase = (unsigned)__cvta_generic_to_shared(ss_smem_bits + SMEM_GUARD);
@@ -394,37 +357,8 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_pull(Dev d, int variant,
     }
   }
   if (MODE == MODE_FILTERED) cnt.slots = lane_slots;
-  // warp, then block reduction of the counters; one atomic per block and counter
-  __shared__ unsigned long long red[4][PULL_THREADS / 32];
-  unsigned long long v[4] = {cnt.nw, cnt.deg, cnt.slots, cnt.act};
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v[i] += __shfl_down_sync(SS_FULL_MASK, v[i], off);
-    if (lane == 0) red[i][threadIdx.x >> 5] = v[i];
-  }
-  __syncthreads();
-  if (threadIdx.x < 4) {
-    unsigned long long s = 0;
-#pragma unroll
-    for (int w = 0; w < PULL_THREADS / 32; ++w) s += red[threadIdx.x][w];
-    if (s) {
-      unsigned long long* dst = threadIdx.x == 0 ? &d.ctl->new_count
-                              : threadIdx.x == 1 ? &d.ctl->new_deg
-                              : threadIdx.x == 2 ? &d.ctl->slots
-                                                 : &d.ctl->active;
-      atomicAdd(dst, s);
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned prev = atomicAdd(&d.ctl->blocks_done, 1u);
-    if (prev == gridDim.x - 1) {
-      __threadfence();
-      iteration_tail(d, variant, cond, use_cond);
-    }
-  }
+  finish_iteration_block<PULL_THREADS>(d, cnt.nw, cnt.deg, cnt.slots, cnt.act, cnt.maxdeg,
+                                       IterLaunch{variant, cond, use_cond});
 }
 
 __global__ void k_init(Dev d) {
@@ -440,6 +374,12 @@ __global__ void k_init(Dev d) {
     d.xacc[s] = 0.0f;
     d.xpar[s] = -1;
   }
+  if (d.ctl->error) {  // a previous run stopped early: restore the push scratch invariants
+    for (long long r = t0; r < d.n_pad; r += stride) {
+      d.pbest[r] = -1;
+      d.psum[r] = 0.0f;
+    }
+  }
 }
 
 __global__ void k_init_root(Dev d, int root) {
@@ -452,7 +392,13 @@ __global__ void k_init_root(Dev d, int root) {
   c->k = 1; c->done = 0; c->error = 0; c->variant = -1;
   c->new_count = 0; c->new_deg = 0; c->slots = 0; c->active = 0;
   c->reached = 1; c->reached_deg = (unsigned long long)d.rdeg[r];
-  c->total_slots = 0; c->dp_slots = 0; c->blocks_done = 0; c->prev_slots = ~0ull;
+  c->total_slots = 0; c->dp_slots = 0; c->blocks_done = 0;
+  c->prev_variant = -1; c->prev_slots = 0; c->prev_new = 1; c->prev_deg = (unsigned long long)d.rdeg[r];
+  c->prev2_new = 0; c->prev_active = 0; c->new_maxdeg = 0; c->prev_maxdeg = (unsigned)d.rdeg[r];
+  c->list_level = 0; c->list_len[0] = 1; c->list_len[1] = 0; c->units = 0; c->push_new = 0;
+  for (int v = 0; v < 4; ++v) c->variant_count[v] = 0;
+  c->loop_guard = 0;
+  d.flist[0][0] = r;
   ss_iter_stats s;
   s.frontier = 1; s.frontier_degree = d.rdeg[r]; s.slots = 0; s.active_chunks = 0;
   s.variant = -1; s.kernel_ns = 0;
@@ -582,12 +528,6 @@ __global__ void k_output(Dev d, int* dist, int* parent) {
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-struct IterLaunch {
-  int variant;
-  cudaGraphConditionalHandle cond;
-  int use_cond;
-};
-
 template <int SR, int C, int MODE>
 static ss_status launch_pull(const slimsell_graph* h, const Dev& d, const IterLaunch& il,
                              cudaStream_t st) {
@@ -634,13 +574,51 @@ static ss_status launch_iteration(const slimsell_graph* h, const Dev& d, int sr,
   }
 }
 
-// Device-side iteration loop: a graph holding one conditional WHILE node whose
-// body is the iteration kernel; the kernel's last block sets the condition.
-// Built once per (semiring, mode, staged-prefix size) and cached in the handle.
-static ss_status loop_graph(slimsell_graph* h, const Dev& d, int sr, int mode, int variant,
+// Queue the kernels of one iteration of the given variant.
+static ss_status launch_variant(const slimsell_graph* h, const Dev& d, int sr, int variant,
+                                const IterLaunch& il, cudaStream_t st) {
+  switch (variant) {
+    case VAR_FULL: return launch_iteration(h, d, sr, MODE_FULL, il, st);
+    case VAR_SLIMWORK: return launch_iteration(h, d, sr, MODE_SLIMWORK, il, st);
+    case VAR_PUSH: return launch_push(h, d, sr, il, st);
+    default: return launch_iteration(h, d, sr, MODE_FILTERED, il, st);
+  }
+}
+
+// Policies that choose the variant on the device before every iteration.
+static bool adaptive(int policy) {
+  return policy == SS_V_PUSH || policy == SS_V_HEURISTIC || policy == SS_V_LEARNED;
+}
+
+// Capture the kernels of one variant into graph g (a conditional body).
+static ss_status capture_into(slimsell_graph* h, const Dev& d, int sr, int variant,
+                              const IterLaunch& il, cudaGraph_t g) {
+  cudaStream_t cs = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e == cudaSuccess)
+    e = cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) {
+    if (cs) cudaStreamDestroy(cs);
+    return cuda_fail(e, "cudaStreamBeginCaptureToGraph");
+  }
+  ss_status s = launch_variant(h, d, sr, variant, il, cs);
+  cudaGraph_t captured = nullptr;
+  e = cudaStreamEndCapture(cs, &captured);
+  cudaStreamDestroy(cs);
+  if (s != SS_OK) return s;
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  return SS_OK;
+}
+
+// Device-side iteration loop: one conditional WHILE node whose body is either
+// the fixed variant's kernels, or (adaptive policies) the decide kernel
+// followed by a SWITCH node over the four variants.  The last block of each
+// iteration's final kernel sets the WHILE condition.  Built once per
+// (semiring, policy, staged-prefix size) and cached in the handle.
+static ss_status loop_graph(slimsell_graph* h, const Dev& d, int sr, int policy,
                             cudaGraphExec_t* out) {
-  cudaGraphExec_t& slot = h->loop_exec[sr][mode];
-  if (slot && h->loop_smem_words[sr][mode] == d.smem_words) {
+  cudaGraphExec_t& slot = h->loop_exec[sr][policy];
+  if (slot && h->loop_smem_words[sr][policy] == d.smem_words) {
     *out = slot;
     return SS_OK;
   }
@@ -650,49 +628,53 @@ static ss_status loop_graph(slimsell_graph* h, const Dev& d, int sr, int mode, i
   }
   cudaGraph_t g = nullptr;
   SS_CUDA(cudaGraphCreate(&g, 0));
-  cudaGraphConditionalHandle cond;
-  cudaError_t e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
-  if (e != cudaSuccess) {
-    cudaGraphDestroy(g);
-    return cuda_fail(e, "cudaGraphConditionalHandleCreate");
+  ss_status s = SS_OK;
+  cudaError_t e;
+  cudaGraphConditionalHandle cw;
+  cudaGraphNodeParams wp = {};
+  cudaGraphNode_t wnode;
+  e = cudaGraphConditionalHandleCreate(&cw, g, 1, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) {
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = cw;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    e = cudaGraphAddNode(&wnode, g, nullptr, nullptr, 0, &wp);
   }
-  cudaGraphNodeParams p = {};
-  p.type = cudaGraphNodeTypeConditional;
-  p.conditional.handle = cond;
-  p.conditional.type = cudaGraphCondTypeWhile;
-  p.conditional.size = 1;
-  cudaGraphNode_t node;
-  e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &p);
-  if (e != cudaSuccess) {
-    cudaGraphDestroy(g);
-    return cuda_fail(e, "cudaGraphAddNode(conditional)");
+  if (e != cudaSuccess) s = cuda_fail(e, "conditional WHILE node");
+  if (s == SS_OK) {
+    cudaGraph_t body = wp.conditional.phGraph_out[0];
+    if (!adaptive(policy)) {
+      s = capture_into(h, d, sr, policy, IterLaunch{policy, cw, 1}, body);
+    } else {
+      cudaGraphConditionalHandle csw;
+      cudaGraphNode_t dnode, snode;
+      cudaGraphNodeParams sp = {};
+      e = cudaGraphConditionalHandleCreate(&csw, body, 0, 0);
+      if (e != cudaSuccess) s = cuda_fail(e, "cudaGraphConditionalHandleCreate(switch)");
+      if (s == SS_OK) s = add_decide_node(h, d, policy, csw, cw, body, &dnode);
+      if (s == SS_OK) {
+        sp.type = cudaGraphNodeTypeConditional;
+        sp.conditional.handle = csw;
+        sp.conditional.type = cudaGraphCondTypeSwitch;
+        sp.conditional.size = 4;
+        e = cudaGraphAddNode(&snode, body, &dnode, nullptr, 1, &sp);
+        if (e != cudaSuccess) s = cuda_fail(e, "conditional SWITCH node");
+      }
+      for (int v = 0; v < 4 && s == SS_OK; ++v)
+        s = capture_into(h, d, sr, v, IterLaunch{v, cw, 1}, sp.conditional.phGraph_out[v]);
+    }
   }
-  cudaGraph_t body = p.conditional.phGraph_out[0];
-  cudaStream_t cs = nullptr;
-  e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
-                                                          cudaStreamCaptureModeRelaxed);
-  if (e != cudaSuccess) {
-    if (cs) cudaStreamDestroy(cs);
-    cudaGraphDestroy(g);
-    return cuda_fail(e, "cudaStreamBeginCaptureToGraph");
+  if (s == SS_OK) {
+    e = cudaGraphInstantiate(&slot, g, 0);
+    if (e != cudaSuccess) {
+      slot = nullptr;
+      s = cuda_fail(e, "cudaGraphInstantiate");
+    }
   }
-  IterLaunch il{variant, cond, 1};
-  ss_status s = launch_iteration(h, d, sr, mode, il, cs);
-  cudaGraph_t captured = nullptr;
-  e = cudaStreamEndCapture(cs, &captured);
-  cudaStreamDestroy(cs);
-  if (s != SS_OK || e != cudaSuccess) {
-    cudaGraphDestroy(g);
-    return s != SS_OK ? s : cuda_fail(e, "cudaStreamEndCapture");
-  }
-  e = cudaGraphInstantiate(&slot, g, 0);
   cudaGraphDestroy(g);
-  if (e != cudaSuccess) {
-    slot = nullptr;
-    return cuda_fail(e, "cudaGraphInstantiate");
-  }
-  h->loop_smem_words[sr][mode] = d.smem_words;
+  if (s != SS_OK) return s;
+  h->loop_smem_words[sr][policy] = d.smem_words;
   *out = slot;
   return SS_OK;
 }
@@ -764,14 +746,6 @@ ss_status slimsell_bfs(slimsell_handle h, int32_t root, int32_t semiring, int32_
     set_error("slimsell_bfs: unknown policy %d", policy);
     return SS_ERR_INVALID;
   }
-  int mode;
-  if (policy == SS_V_FULL) mode = MODE_FULL;
-  else if (policy == SS_V_SLIMWORK) mode = MODE_SLIMWORK;
-  else if (policy == SS_V_PULL_FILTERED) mode = MODE_FILTERED;
-  else {
-    set_error("slimsell_bfs: policy %d not available in this build", policy);
-    return SS_ERR_UNSUPPORTED;
-  }
   cudaStream_t st = (cudaStream_t)stream;
   const Dev d = h->dev();
   const int grid = 8 * h->num_sms;
@@ -789,19 +763,27 @@ ss_status slimsell_bfs(slimsell_handle h, int32_t root, int32_t semiring, int32_
 
   if (device_loop) {
     cudaGraphExec_t exec = nullptr;
-    ss_status s = loop_graph(h, d, semiring, mode, policy, &exec);
+    ss_status s = loop_graph(h, d, semiring, policy, &exec);
     if (s != SS_OK) return s;
     SS_CUDA(cudaGraphLaunch(exec, st));
   } else {
-    const IterLaunch il{policy, 0, 0};
     const long long max_iter = (long long)h->n + 2;
     for (long long it = 0;; ++it) {
       if (it > max_iter) {
         set_error("slimsell_bfs: no convergence after %lld iterations", it);
         return SS_ERR_CUDA;
       }
+      // the decide kernel logs the iteration's features; adaptive policies read its choice
+      ss_status s = launch_decide(h, d, policy, 0, 0, st);
+      if (s != SS_OK) return s;
+      int variant = policy;
+      if (adaptive(policy)) {
+        SS_CUDA(cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+        SS_CUDA(cudaStreamSynchronize(st));
+        variant = h->h_ctl->variant;
+      }
       if (prof) SS_CUDA(cudaEventRecord(h->ev_a, st));
-      ss_status s = launch_iteration(h, d, semiring, mode, il, st);
+      s = launch_variant(h, d, semiring, variant, IterLaunch{variant, 0, 0}, st);
       if (s != SS_OK) return s;
       if (prof) SS_CUDA(cudaEventRecord(h->ev_b, st));
       SS_CUDA(cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));

@@ -537,8 +537,20 @@ static ss_status alloc_state(slimsell_graph* h) {
   if ((s = dmalloc(h, (void**)&h->xacc, sizeof(float) * ns * h->C)) != SS_OK) return s;
   if ((s = dmalloc(h, (void**)&h->xpar, sizeof(int) * ns * h->C)) != SS_OK) return s;
   if ((s = dmalloc(h, (void**)&h->arrive, sizeof(unsigned) * ns)) != SS_OK) return s;
+  for (int b = 0; b < 2; ++b)
+    if ((s = dmalloc(h, (void**)&h->flist[b], sizeof(int) * np)) != SS_OK) return s;
+  h->units_cap = (long long)np + h->nnz / 256 + 1024;  // any frontier fits
+  if ((s = dmalloc(h, (void**)&h->units, sizeof(int2) * (size_t)h->units_cap)) != SS_OK) return s;
+  if ((s = dmalloc(h, (void**)&h->pbest, sizeof(int) * np)) != SS_OK) return s;
+  if ((s = dmalloc(h, (void**)&h->psum, sizeof(float) * np)) != SS_OK) return s;
+  if ((s = dmalloc(h, (void**)&h->touched, sizeof(unsigned) * (size_t)h->fb_words)) != SS_OK) return s;
+  SS_CUDA(cudaMemset(h->pbest, 0xff, sizeof(int) * np));
+  SS_CUDA(cudaMemset(h->psum, 0, sizeof(float) * np));
+  SS_CUDA(cudaMemset(h->touched, 0, sizeof(unsigned) * (size_t)h->fb_words));
   if ((s = dmalloc(h, (void**)&h->ctl, sizeof(Ctl))) != SS_OK) return s;
   h->iter_cap = 1 << 16;
+  if ((s = dmalloc(h, (void**)&h->feats, sizeof(float) * SS_SELECTOR_FEATURES * (size_t)h->iter_cap)) != SS_OK)
+    return s;
   if ((s = dmalloc(h, (void**)&h->iters, sizeof(ss_iter_stats) * (size_t)h->iter_cap)) != SS_OK) return s;
   SS_CUDA(cudaMemset(h->arrive, 0, sizeof(unsigned) * ns));
   SS_CUDA(cudaMemset(h->fb[0], 0, sizeof(unsigned) * (size_t)h->fb_words));
@@ -557,7 +569,8 @@ void free_handle(slimsell_graph* h) {
   if (!h) return;
   void* ptrs[] = {h->perm, h->invperm, h->rdeg, h->cl, h->cs, h->col, h->items, h->split_n,
                   h->lvl, h->act, h->fb[0], h->fb[1], h->fr, h->par, h->xacc, h->xpar,
-                  h->arrive, h->ctl, h->iters};
+                  h->arrive, h->ctl, h->iters, h->flist[0], h->flist[1], h->units, h->pbest,
+                  h->psum, h->touched, h->mlp, h->feats};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->h_ctl) cudaFreeHost(h->h_ctl);
@@ -588,6 +601,9 @@ ss::Dev slimsell_graph::dev() const {
   long long cap = (long long)(smem_bytes / 16) * 4;
   d.smem_words = (int)(need < cap ? need : cap);
   d.fr = fr; d.par = par; d.xacc = xacc; d.xpar = xpar; d.arrive = arrive;
+  d.flist[0] = flist[0]; d.flist[1] = flist[1]; d.units = units; d.units_cap = units_cap;
+  d.pbest = pbest; d.psum = psum; d.touched = touched; d.mlp = mlp; d.feats = feats;
+  d.nnz = nnz; d.total_slots = slots;
   d.ctl = ctl; d.iters = iters; d.iter_cap = iter_cap;
   return d;
 }

@@ -42,8 +42,21 @@ struct Ctl {
   unsigned long long total_slots; // cumulative slots
   unsigned long long dp_slots;    // slots read by the DP pass
   unsigned int blocks_done;       // blocks of the current iteration kernel that finished
-  unsigned int pad0;
-  unsigned long long prev_slots;  // slots read by the previous iteration (staging decision)
+  int prev_variant;               // variant of the previous iteration (-1 before the first)
+  unsigned long long prev_slots;  // slots read by the previous iteration
+  unsigned long long prev_new;    // |f_{k-1}|: vertices discovered by the previous iteration
+  unsigned long long prev_deg;    // their degree sum (frontier edges)
+  unsigned long long prev2_new;   // |f_{k-2}|
+  unsigned long long prev_active; // chunks processed by the previous iteration
+  unsigned int new_maxdeg;        // largest degree discovered by the current iteration
+  unsigned int prev_maxdeg;       // ... by the previous iteration
+  int list_level;                 // level whose vertex list is in flist (-1: none)
+  int pad1;
+  unsigned long long list_len[2]; // vertex-list lengths, by level parity
+  unsigned long long units;       // push work units queued by the current iteration
+  unsigned long long push_new;    // vertices first touched by the current push
+  unsigned long long variant_count[4];  // iterations run with each variant
+  unsigned long long loop_guard;  // decide-kernel executions in this run (device loop bound)
 };
 
 // Flat view of the handle's device buffers handed to kernels by value.
@@ -67,6 +80,15 @@ struct Dev {
   float* xacc;          // [n_split * C] SlimChunk partial sums (real semiring)
   int* xpar;            // [n_split * C] SlimChunk partial parents (original id, -1 = none)
   unsigned* arrive;     // [n_split] SlimChunk arrival counters
+  int* flist[2];        // [n_pad] vertex lists of a level (push iterations), by level parity
+  int2* units;          // [units_cap] push work units (row, first neighbour index)
+  long long units_cap;
+  int* pbest;           // [n_pad] push: largest frontier-neighbour original id (-1 = none)
+  float* psum;          // [n_pad] push: real-semiring sum of frontier-neighbour values
+  unsigned* touched;    // [fb_words] push: rows reached by the current push
+  const float* mlp;     // selector weights (16-64-64-4 MLP), or NULL
+  float* feats;         // [iter_cap][16] selector features of each iteration of the last run
+  long long nnz, total_slots;
   Ctl* ctl;
   ss_iter_stats* iters; // [iter_cap]
   int iter_cap;
@@ -99,6 +121,14 @@ struct slimsell_graph {
   float* xacc = nullptr;
   int* xpar = nullptr;
   unsigned* arrive = nullptr;
+  int* flist[2] = {nullptr, nullptr};
+  int2* units = nullptr;
+  long long units_cap = 0;
+  int* pbest = nullptr;
+  float* psum = nullptr;
+  unsigned* touched = nullptr;
+  float* mlp = nullptr;       // selector weights on the device (NULL until loaded)
+  float* feats = nullptr;
   int smem_bytes = SS_SMEM_MAX_BYTES;  // bitmap prefix staged in shared memory
   int dp_pass = 0;                     // 1: parents by a separate DP pass after the iterations
   ss::Ctl* ctl = nullptr;
@@ -113,8 +143,8 @@ struct slimsell_graph {
   cudaEvent_t ev_done = nullptr;       // end of the last call's work on its stream
   int pending = 0;                     // last-run statistics not yet read back
   int device_loop = 1;                 // iterate with a conditional CUDA graph
-  cudaGraphExec_t loop_exec[4][4] = {};  // [semiring][mode] device-side iteration loops
-  int loop_smem_words[4][4] = {};
+  cudaGraphExec_t loop_exec[4][6] = {};  // [semiring][policy] device-side iteration loops
+  int loop_smem_words[4][6] = {};
   std::vector<int> iter_ns;            // per-iteration kernel time of the last profiled call
 
   ss::Dev dev() const;

@@ -1,0 +1,141 @@
+// Device-side pieces shared by the iteration kernels (pull, push) and the driver.
+#pragma once
+
+#include "ss_common.cuh"
+
+namespace ss {
+
+// Variant ids executed by one iteration (the values of ss_policy 0..3).
+enum { VAR_FULL = SS_V_FULL, VAR_SLIMWORK = SS_V_SLIMWORK, VAR_PUSH = SS_V_PUSH,
+       VAR_FILTERED = SS_V_PULL_FILTERED };
+
+struct IterLaunch {
+  int variant;
+  cudaGraphConditionalHandle cond;  // WHILE-loop condition of the device-side loop
+  int use_cond;
+};
+
+// End of an iteration, run by the last block of its final kernel: record the
+// statistics, test convergence, advance k and (device-side loop) set the loop
+// condition.  The loop also stops, flagging an error, if k passes n + 1 or more
+// than n vertices were counted, which a correct BFS never does, so the device
+// loop always terminates.
+__device__ __forceinline__ void iteration_tail(const Dev& d, int variant,
+                                               cudaGraphConditionalHandle cond, int use_cond) {
+  Ctl* c = d.ctl;
+  const int k = c->k;
+  const unsigned long long nc = atomicAdd(&c->new_count, 0ull);
+  const unsigned long long nd = atomicAdd(&c->new_deg, 0ull);
+  const unsigned long long sl = atomicAdd(&c->slots, 0ull);
+  const unsigned long long ac = atomicAdd(&c->active, 0ull);
+  const unsigned md = atomicMax(&c->new_maxdeg, 0u);
+  if (k < d.iter_cap) {
+    ss_iter_stats s;
+    s.frontier = (long long)nc;
+    s.frontier_degree = (long long)nd;
+    s.slots = (long long)sl;
+    s.active_chunks = (long long)ac;
+    s.variant = variant;
+    s.kernel_ns = 0;
+    d.iters[k] = s;
+  }
+  c->reached += nc;
+  c->reached_deg += nd;
+  c->total_slots += sl;
+  c->prev_slots = sl;
+  c->prev2_new = c->prev_new;
+  c->prev_new = nc;
+  c->prev_deg = nd;
+  c->prev_active = ac;
+  c->prev_maxdeg = md;
+  c->prev_variant = variant;
+  c->variant = variant;
+  if (variant >= 0 && variant < 4) c->variant_count[variant] += 1;
+  if (variant == VAR_PUSH) {  // the touched list is the vertex list of level k
+    c->list_len[k & 1] = nc;
+    c->list_level = k;
+  } else {
+    c->list_level = -1;
+  }
+  c->push_new = 0;
+  c->units = 0;
+  bool stop = (nc == 0);
+  if (k >= d.n + 1 || c->reached > (unsigned long long)d.n) {
+    c->error |= 1;
+    stop = true;
+  }
+  if (stop) c->done = 1;
+  c->new_count = 0;
+  c->new_deg = 0;
+  c->slots = 0;
+  c->active = 0;
+  c->new_maxdeg = 0;
+  c->k = k + 1;
+  c->blocks_done = 0;
+  __threadfence();
+  if (use_cond) cudaGraphSetConditional(cond, stop ? 0u : 1u);
+}
+
+// Block-wide reduction of a kernel's counters (new vertices, their degree sum,
+// slots read, chunks processed, largest new degree), one atomic per block and
+// counter; the last block to finish runs the iteration tail.  All threads call.
+template <int THREADS>
+__device__ __forceinline__ void finish_iteration_block(const Dev& d, unsigned long long nw,
+                                                       unsigned long long deg, unsigned long long slots,
+                                                       unsigned long long act, unsigned maxdeg,
+                                                       const IterLaunch& il) {
+  __shared__ unsigned long long red[4][THREADS / 32];
+  __shared__ unsigned redmax[THREADS / 32];
+  const int lane = threadIdx.x & 31;
+  unsigned long long v[4] = {nw, deg, slots, act};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v[i] += __shfl_down_sync(SS_FULL_MASK, v[i], off);
+    if (lane == 0) red[i][threadIdx.x >> 5] = v[i];
+  }
+  maxdeg = __reduce_max_sync(SS_FULL_MASK, maxdeg);
+  if (lane == 0) redmax[threadIdx.x >> 5] = maxdeg;
+  __syncthreads();
+  if (threadIdx.x < 5) {
+    if (threadIdx.x < 4) {
+      unsigned long long s = 0;
+#pragma unroll
+      for (int w = 0; w < THREADS / 32; ++w) s += red[threadIdx.x][w];
+      if (s) {
+        unsigned long long* dst = threadIdx.x == 0 ? &d.ctl->new_count
+                                : threadIdx.x == 1 ? &d.ctl->new_deg
+                                : threadIdx.x == 2 ? &d.ctl->slots
+                                                   : &d.ctl->active;
+        atomicAdd(dst, s);
+      }
+    } else {
+      unsigned m = 0;
+#pragma unroll
+      for (int w = 0; w < THREADS / 32; ++w) m = max(m, redmax[w]);
+      if (m) atomicMax(&d.ctl->new_maxdeg, m);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned prev = atomicAdd(&d.ctl->blocks_done, 1u);
+    if (prev == gridDim.x - 1) {
+      __threadfence();
+      iteration_tail(d, il.variant, il.cond, il.use_cond);
+    }
+  }
+}
+
+// Launchers implemented in the other translation units.
+ss_status launch_push(const slimsell_graph* h, const Dev& d, int sr, const IterLaunch& il,
+                      cudaStream_t st);
+ss_status launch_pull_variant(const slimsell_graph* h, const Dev& d, int sr, int variant,
+                              const IterLaunch& il, cudaStream_t st);
+ss_status launch_decide(const slimsell_graph* h, const Dev& d, int policy,
+                        cudaGraphConditionalHandle sw, int use_sw, cudaStream_t st);
+ss_status add_decide_node(const slimsell_graph* h, const Dev& d, int policy,
+                          cudaGraphConditionalHandle sw, cudaGraphConditionalHandle cw,
+                          cudaGraph_t g, cudaGraphNode_t* out);
+
+}  // namespace ss

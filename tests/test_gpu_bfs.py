@@ -46,7 +46,7 @@ def check_stats(G, g, r, sr):
 
 
 @pytest.mark.parametrize("sr", SEMIRINGS)
-@pytest.mark.parametrize("pol", ["full", "slimwork", "pull_filtered"])
+@pytest.mark.parametrize("pol", ["full", "slimwork", "pull_filtered", "push", "heuristic"])
 def test_kron14_parity(sr, pol):
     """Kronecker scale 14, C = 32, sigma = n (the small configuration), several roots."""
     g = gg.kronecker(14, seed=1)
@@ -132,7 +132,7 @@ def test_device_loop_matches_host_loop():
     for r in gg.roots(g, 3, seed=7):
         d, p = expected(g, r)
         for sr in SEMIRINGS:
-            for pol in ("full", "slimwork", "pull_filtered"):
+            for pol in ("full", "slimwork", "pull_filtered", "push", "heuristic"):
                 res = []
                 for loop in (1, 0):
                     G.set_option(ss.OPT_DEVICE_LOOP, loop)
@@ -163,7 +163,7 @@ def test_edge_cases():
             for r in sorted({0, g.n - 1, g.n // 2}):
                 d, p = expected(g, r)
                 for sr in SEMIRINGS:
-                    for pol in ("full", "slimwork", "pull_filtered"):
+                    for pol in ("full", "slimwork", "pull_filtered", "push", "heuristic"):
                         dist, parent = run(G, r, sr, pol)
                         np.testing.assert_array_equal(dist, d, err_msg=f"{g.name} {sr} {pol} r={r}")
                         np.testing.assert_array_equal(parent, p, err_msg=f"{g.name} {sr} {pol}")
@@ -207,11 +207,13 @@ def test_invalid_arguments_on_gpu():
         ss.slimsell_bfs(G.h, 0, 7, 1, dist, None)
     with pytest.raises(ss.SlimSellError):
         ss.slimsell_bfs(G.h, 0, 0, 99, dist, None)
+    with pytest.raises(ss.SlimSellError):
+        ss.slimsell_selector_load(G.h, np.zeros(10, dtype=np.float32))
     G.close()
 
 
 @pytest.mark.parametrize("sr", SEMIRINGS)
-@pytest.mark.parametrize("pol", ["slimwork", "pull_filtered"])
+@pytest.mark.parametrize("pol", ["slimwork", "pull_filtered", "heuristic"])
 def test_kron22_sampled_parity(sr, pol):
     """Full-size Kronecker scale 22 (the main benchmark graph), 2 roots, SlimWork + SlimChunk."""
     g = _kron22()
