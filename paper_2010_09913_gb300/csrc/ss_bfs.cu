@@ -395,10 +395,9 @@ __global__ void k_init_root(Dev d, int root) {
   c->total_slots = 0; c->dp_slots = 0; c->blocks_done = 0;
   c->prev_variant = -1; c->prev_slots = 0; c->prev_new = 1; c->prev_deg = (unsigned long long)d.rdeg[r];
   c->prev2_new = 0; c->prev_active = 0; c->new_maxdeg = 0; c->prev_maxdeg = (unsigned)d.rdeg[r];
-  c->list_level = 0; c->list_len[0] = 1; c->list_len[1] = 0; c->units = 0; c->push_new = 0;
+  c->units = 0;
   for (int v = 0; v < 4; ++v) c->variant_count[v] = 0;
   c->loop_guard = 0;
-  d.flist[0][0] = r;
   ss_iter_stats s;
   s.frontier = 1; s.frontier_degree = d.rdeg[r]; s.slots = 0; s.active_chunks = 0;
   s.variant = -1; s.kernel_ns = 0;

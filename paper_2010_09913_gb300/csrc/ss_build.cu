@@ -537,8 +537,6 @@ static ss_status alloc_state(slimsell_graph* h) {
   if ((s = dmalloc(h, (void**)&h->xacc, sizeof(float) * ns * h->C)) != SS_OK) return s;
   if ((s = dmalloc(h, (void**)&h->xpar, sizeof(int) * ns * h->C)) != SS_OK) return s;
   if ((s = dmalloc(h, (void**)&h->arrive, sizeof(unsigned) * ns)) != SS_OK) return s;
-  for (int b = 0; b < 2; ++b)
-    if ((s = dmalloc(h, (void**)&h->flist[b], sizeof(int) * np)) != SS_OK) return s;
   h->units_cap = (long long)np + h->nnz / 256 + 1024;  // any frontier fits
   if ((s = dmalloc(h, (void**)&h->units, sizeof(int2) * (size_t)h->units_cap)) != SS_OK) return s;
   if ((s = dmalloc(h, (void**)&h->pbest, sizeof(int) * np)) != SS_OK) return s;
@@ -569,7 +567,7 @@ void free_handle(slimsell_graph* h) {
   if (!h) return;
   void* ptrs[] = {h->perm, h->invperm, h->rdeg, h->cl, h->cs, h->col, h->items, h->split_n,
                   h->lvl, h->act, h->fb[0], h->fb[1], h->fr, h->par, h->xacc, h->xpar,
-                  h->arrive, h->ctl, h->iters, h->flist[0], h->flist[1], h->units, h->pbest,
+                  h->arrive, h->ctl, h->iters, h->units, h->pbest,
                   h->psum, h->touched, h->mlp, h->feats};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -601,7 +599,7 @@ ss::Dev slimsell_graph::dev() const {
   long long cap = (long long)(smem_bytes / 16) * 4;
   d.smem_words = (int)(need < cap ? need : cap);
   d.fr = fr; d.par = par; d.xacc = xacc; d.xpar = xpar; d.arrive = arrive;
-  d.flist[0] = flist[0]; d.flist[1] = flist[1]; d.units = units; d.units_cap = units_cap;
+  d.units = units; d.units_cap = units_cap;
   d.pbest = pbest; d.psum = psum; d.touched = touched; d.mlp = mlp; d.feats = feats;
   d.nnz = nnz; d.total_slots = slots;
   d.ctl = ctl; d.iters = iters; d.iter_cap = iter_cap;

@@ -50,11 +50,7 @@ struct Ctl {
   unsigned long long prev_active; // chunks processed by the previous iteration
   unsigned int new_maxdeg;        // largest degree discovered by the current iteration
   unsigned int prev_maxdeg;       // ... by the previous iteration
-  int list_level;                 // level whose vertex list is in flist (-1: none)
-  int pad1;
-  unsigned long long list_len[2]; // vertex-list lengths, by level parity
   unsigned long long units;       // push work units queued by the current iteration
-  unsigned long long push_new;    // vertices first touched by the current push
   unsigned long long variant_count[4];  // iterations run with each variant
   unsigned long long loop_guard;  // decide-kernel executions in this run (device loop bound)
 };
@@ -80,7 +76,6 @@ struct Dev {
   float* xacc;          // [n_split * C] SlimChunk partial sums (real semiring)
   int* xpar;            // [n_split * C] SlimChunk partial parents (original id, -1 = none)
   unsigned* arrive;     // [n_split] SlimChunk arrival counters
-  int* flist[2];        // [n_pad] vertex lists of a level (push iterations), by level parity
   int2* units;          // [units_cap] push work units (row, first neighbour index)
   long long units_cap;
   int* pbest;           // [n_pad] push: largest frontier-neighbour original id (-1 = none)
@@ -121,7 +116,6 @@ struct slimsell_graph {
   float* xacc = nullptr;
   int* xpar = nullptr;
   unsigned* arrive = nullptr;
-  int* flist[2] = {nullptr, nullptr};
   int2* units = nullptr;
   long long units_cap = 0;
   int* pbest = nullptr;

@@ -51,13 +51,6 @@ __device__ __forceinline__ void iteration_tail(const Dev& d, int variant,
   c->prev_variant = variant;
   c->variant = variant;
   if (variant >= 0 && variant < 4) c->variant_count[variant] += 1;
-  if (variant == VAR_PUSH) {  // the touched list is the vertex list of level k
-    c->list_len[k & 1] = nc;
-    c->list_level = k;
-  } else {
-    c->list_level = -1;
-  }
-  c->push_new = 0;
   c->units = 0;
   bool stop = (nc == 0);
   if (k >= d.n + 1 || c->reached > (unsigned long long)d.n) {

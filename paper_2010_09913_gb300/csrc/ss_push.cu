@@ -5,16 +5,17 @@
 // sum of frontier values -- by scattering from the frontier instead of
 // gathering into every row:
 //
-//   k_push_expand   clears fb[k&1] (it holds level k-2) and the touched map,
-//                   and turns each level-(k-1) vertex into work units of
-//                   PUSH_UNIT neighbours (from the previous push's vertex list,
-//                   or from the bitmap after a pull iteration);
+//   k_push_expand   clears the touched map and turns each level-(k-1) vertex
+//                   (read from the frontier bitmap) into work units of
+//                   PUSH_UNIT neighbours;
 //   k_push_scatter  one warp per unit reads the vertex's row (column-major, so
 //                   with stride C) and, for every unvisited neighbour, folds in
-//                   the parent by atomicMax and the real value by atomicAdd;
-//                   the first touch of a row appends it to the level-k list;
-//   k_push_post     gives listed rows level k, parent, value and frontier bit,
-//                   resets the scratch, and runs the iteration tail.
+//                   the parent by atomicMax, the real value by atomicAdd and a
+//                   touched bit by atomicOr (reductions: no result is read);
+//   k_push_post     walks the touched words: a touched word becomes the
+//                   frontier word of level k (fb[k&1] held level k-2, which is
+//                   overwritten), and each touched row gets level k, parent and
+//                   value; the scratch is reset and the iteration tail runs.
 #include "ss_device.cuh"
 
 namespace ss {
@@ -52,35 +53,21 @@ __global__ void __launch_bounds__(PUSH_THREADS) k_push_expand(Dev d) {
   const int lane = threadIdx.x & 31;
   const long long stride = (long long)gridDim.x * blockDim.x;
   const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  unsigned* fbk = d.fb[k & 1];
-  for (long long w = t0; w < d.fb_words; w += stride) {
-    fbk[w] = 0u;
-    d.touched[w] = 0u;
-  }
-  const long long wstride = stride & ~31LL;  // whole warps walk the inputs together
-  const long long w0 = t0 - lane;
-  if (c->list_level == k - 1) {
-    const int* list = d.flist[(k - 1) & 1];
-    const long long len = (long long)c->list_len[(k - 1) & 1];
-    for (long long i0 = w0; i0 < len; i0 += wstride) {
-      const long long i = i0 + lane;
-      emit_units(d, i < len ? list[i] : -1, lane);
-    }
-  } else {
-    const unsigned* fbm = d.fb[(k - 1) & 1];
-    const long long words = ((long long)d.n_pad + 31) / 32;
-    for (long long i0 = w0; i0 < words; i0 += wstride) {
-      const long long i = i0 + lane;
-      unsigned bits = i < words ? fbm[i] : 0u;
-      while (__any_sync(SS_FULL_MASK, bits != 0u)) {
-        int u = -1;
-        if (bits) {
-          const int b = __ffs(bits) - 1;
-          bits &= bits - 1;
-          u = (int)(i * 32 + b);
-        }
-        emit_units(d, u, lane);
+  const long long words = ((long long)d.n_pad + 31) / 32;
+  for (long long w = t0; w < words; w += stride) d.touched[w] = 0u;
+  const long long wstride = stride & ~31LL;  // whole warps walk the bitmap together
+  const unsigned* fbm = d.fb[(k - 1) & 1];
+  for (long long i0 = t0 - lane; i0 < words; i0 += wstride) {
+    const long long i = i0 + lane;
+    unsigned bits = i < words ? fbm[i] : 0u;
+    while (__any_sync(SS_FULL_MASK, bits != 0u)) {
+      int u = -1;
+      if (bits) {
+        const int b = __ffs(bits) - 1;
+        bits &= bits - 1;
+        u = (int)(i * 32 + b);
       }
+      emit_units(d, u, lane);
     }
   }
 }
@@ -89,12 +76,10 @@ template <int SR, int C>
 __global__ void __launch_bounds__(PUSH_THREADS) k_push_scatter(Dev d) {
   const Ctl* c = d.ctl;
   if (c->done) return;
-  const int k = c->k;
   const long long nunits = min((long long)c->units, d.units_cap);
   const int lane = threadIdx.x & 31;
   const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-  int* list = d.flist[k & 1];
   unsigned long long my_slots = 0;
   for (long long ui = wid; ui < nunits; ui += nw) {
     const int2 un = d.units[ui];
@@ -105,28 +90,17 @@ __global__ void __launch_bounds__(PUSH_THREADS) k_push_scatter(Dev d) {
     const int origu = __ldg(d.perm + u);
     const float val = (SR == SS_REAL) ? d.fr[u] : 0.0f;
     const int jend = min(un.y + PUSH_UNIT, deg);
-    for (int jb = un.y; jb < jend; jb += 32) {  // warp-uniform loop
-      const int j = jb + lane;
-      bool isnew = false;
-      int v = -1;
-      if (j < jend) {
-        v = __ldg(rowp + (long long)j * C);
-        ++my_slots;
-        if (d.lvl[v] == SS_INF) {
-          atomicMax(d.pbest + v, origu);
-          if (SR == SS_REAL) atomicAdd(d.psum + v, val);
-          const unsigned bit = 1u << (v & 31);
-          isnew = !(atomicOr(d.touched + (v >> 5), bit) & bit);
-        }
-      }
-      // warp-aggregated append of first touches to the level-k list
-      const unsigned m = __ballot_sync(SS_FULL_MASK, isnew);
-      if (m) {
-        unsigned long long base = 0;
-        const int leader = __ffs(m) - 1;
-        if (lane == leader) base = atomicAdd(&d.ctl->push_new, (unsigned long long)__popc(m));
-        base = __shfl_sync(SS_FULL_MASK, base, leader);
-        if (isnew) list[base + __popc(m & ((1u << lane) - 1u))] = v;
+    for (int j = un.y + lane; j < jend; j += 32) {
+      const int v = __ldg(rowp + (long long)j * C);
+      ++my_slots;
+      if (d.lvl[v] == SS_INF) {
+        // parents and touched bits only grow, so a stale read can only cause a
+        // redundant atomic, never a missed one
+        if (*(volatile const int*)(d.pbest + v) < origu) atomicMax(d.pbest + v, origu);
+        if (SR == SS_REAL) atomicAdd(d.psum + v, val);
+        const unsigned bit = 1u << (v & 31);
+        if (!(*(volatile const unsigned*)(d.touched + (v >> 5)) & bit))
+          atomicOr(d.touched + (v >> 5), bit);
       }
     }
   }
@@ -147,26 +121,30 @@ __global__ void __launch_bounds__(PUSH_THREADS) k_push_post(Dev d, IterLaunch il
   const Ctl* c = d.ctl;
   if (c->done) return;
   const int k = c->k;
-  const long long cnt = (long long)c->push_new;
-  const int* list = d.flist[k & 1];
   unsigned* fbk = d.fb[k & 1];
+  const long long words = ((long long)d.n_pad + 31) / 32;
   unsigned long long nw = 0, deg = 0;
   unsigned maxdeg = 0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int v = list[i];
-    d.lvl[v] = k;
-    d.par[v] = d.pbest[v] + 1;  // largest-id frontier neighbour + 1
-    d.pbest[v] = -1;
-    if (SR == SS_REAL) {
-      d.fr[v] = d.psum[v];
-      d.psum[v] = 0.0f;
+  for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < words;
+       w += (long long)gridDim.x * blockDim.x) {
+    unsigned bits = d.touched[w];
+    fbk[w] = bits;  // f_k: exactly the rows first reached now
+    while (bits) {
+      const int b = __ffs(bits) - 1;
+      bits &= bits - 1;
+      const int v = (int)(w * 32 + b);
+      d.lvl[v] = k;
+      d.par[v] = d.pbest[v] + 1;  // largest-id frontier neighbour + 1
+      d.pbest[v] = -1;
+      if (SR == SS_REAL) {
+        d.fr[v] = d.psum[v];
+        d.psum[v] = 0.0f;
+      }
+      const int dv = d.rdeg[v];
+      ++nw;
+      deg += (unsigned long long)dv;
+      maxdeg = max(maxdeg, (unsigned)dv);
     }
-    atomicOr(fbk + (v >> 5), 1u << (v & 31));
-    const int dv = d.rdeg[v];
-    ++nw;
-    deg += (unsigned long long)dv;
-    maxdeg = max(maxdeg, (unsigned)dv);
   }
   finish_iteration_block<PUSH_THREADS>(d, nw, deg, 0ull, 0ull, maxdeg, il);
 }
@@ -177,7 +155,7 @@ static ss_status launch_push_c(const slimsell_graph* h, const Dev& d, const Iter
   const int g = 8 * h->num_sms;
   k_push_expand<<<g, PUSH_THREADS, 0, st>>>(d);
   k_push_scatter<SR, C><<<g, PUSH_THREADS, 0, st>>>(d);
-  k_push_post<SR><<<4 * h->num_sms, PUSH_THREADS, 0, st>>>(d, il);
+  k_push_post<SR><<<8 * h->num_sms, PUSH_THREADS, 0, st>>>(d, il);
   SS_CUDA(cudaGetLastError());
   return SS_OK;
 }
