@@ -138,6 +138,25 @@ ss_status slimsell_build(const int64_t* d_row_ptr, const int32_t* d_col, int32_t
 ss_status slimsell_bfs(slimsell_handle h, int32_t root, int32_t semiring, int32_t policy,
                        int32_t* d_dist, int32_t* d_parent, void* stream);
 
+/*
+ * Multi-source BFS (an extension beyond the paper): the boolean semiring of
+ * Section III-A run for k sources at once, frontiers bit-packed as
+ * ceil(k / 64) uint64 words per vertex, rounded up to a power of two and to at
+ * least 32 / C words.
+ *   d_roots  int32[k] device, vertex ids in [0, n) (checked; duplicates allowed).
+ *   k        1 .. 1024.
+ *   policy   SS_V_FULL or SS_V_SLIMWORK (SlimWork skips chunks whose rows
+ *            have every source visited; SlimChunk splitting applies).
+ *   d_dist   int32[n][k] device or NULL: VERTEX-major, d_dist[v * k + s] =
+ *            distance from roots[s] to v, -1 if unreached.
+ * Synchronous (returns when done).  Run statistics: reached = reached
+ * (vertex, source) pairs, reached_degree = their degree sum (= 2 x the sum
+ * over sources of the edges in each source's component).
+ * Errors: SS_ERR_INVALID, SS_ERR_OOM, SS_ERR_CUDA.
+ */
+ss_status slimsell_bfs_multi(slimsell_handle h, const int32_t* d_roots, int32_t k, int32_t policy,
+                             int32_t* d_dist, void* stream);
+
 /* Layout summary. */
 ss_status slimsell_get_info(slimsell_handle h, ss_info* out);
 

@@ -67,6 +67,7 @@ def lib():
     sigs = {
         "slimsell_build": (i32, [_VP, _VP, i32, i64, i32, i32, i32, _VP, ctypes.POINTER(_VP)]),
         "slimsell_bfs": (i32, [_VP, i32, i32, i32, _VP, _VP, _VP]),
+        "slimsell_bfs_multi": (i32, [_VP, _VP, i32, i32, _VP, _VP]),
         "slimsell_get_info": (i32, [_VP, ctypes.POINTER(ss_info)]),
         "slimsell_get_run_stats": (i32, [_VP, ctypes.POINTER(ss_run_stats),
                                          ctypes.POINTER(ss_iter_stats), i32]),
@@ -92,7 +93,7 @@ def lib():
 
 
 def exported_symbols() -> list[str]:
-    return ["slimsell_build", "slimsell_bfs", "slimsell_get_info", "slimsell_get_run_stats",
+    return ["slimsell_build", "slimsell_bfs", "slimsell_bfs_multi", "slimsell_get_info", "slimsell_get_run_stats",
             "slimsell_set_profiling", "slimsell_set_option", "slimsell_export_layout",
             "slimsell_destroy",
             "slimsell_sigma_sort_noalloc", "slimsell_selector_load", "slimsell_get_features",
@@ -135,6 +136,13 @@ def slimsell_bfs(h: int, root: int, semiring: int, policy: int, dist: torch.Tens
     _check("slimsell_bfs", lib().slimsell_bfs(
         h, int(root), int(semiring), int(policy), _ptr(dist, torch.int32, "dist"),
         _ptr(parent, torch.int32, "parent"), _stream(stream)))
+
+
+def slimsell_bfs_multi(h: int, roots: torch.Tensor, policy: int, dist: torch.Tensor | None,
+                       stream=None) -> None:
+    _check("slimsell_bfs_multi", lib().slimsell_bfs_multi(
+        h, _ptr(roots, torch.int32, "roots"), int(roots.numel()), int(policy),
+        _ptr(dist, torch.int32, "dist"), _stream(stream)))
 
 
 def slimsell_get_info(h: int) -> ss_info:
@@ -262,6 +270,16 @@ class SlimSellGraph:
             parent = torch.empty(self.n, dtype=torch.int32, device=dev)
         slimsell_bfs(self.h, root, sr, pol, dist, parent, stream)
         return dist, parent
+
+    def bfs_multi(self, roots, policy="slimwork", dist=None, want_dist: bool = True, stream=None):
+        """k-source BFS; returns dist as an (n, k) int32 tensor (vertex-major)."""
+        pol = POLICIES[policy] if isinstance(policy, str) else int(policy)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        r = torch.as_tensor(roots, dtype=torch.int32).to(dev)
+        if dist is None and want_dist:
+            dist = torch.empty((self.n, r.numel()), dtype=torch.int32, device=dev)
+        slimsell_bfs_multi(self.h, r, pol, dist, stream)
+        return dist
 
     def run_stats(self, cap: int = 0):
         return slimsell_get_run_stats(self.h, cap)

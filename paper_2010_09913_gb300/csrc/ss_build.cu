@@ -568,7 +568,8 @@ void free_handle(slimsell_graph* h) {
   void* ptrs[] = {h->perm, h->invperm, h->rdeg, h->cl, h->cs, h->col, h->items, h->split_n,
                   h->lvl, h->act, h->fb[0], h->fb[1], h->fr, h->par, h->xacc, h->xpar,
                   h->arrive, h->ctl, h->iters, h->units, h->pbest,
-                  h->psum, h->touched, h->mlp, h->feats};
+                  h->psum, h->touched, h->mlp, h->feats, h->mF[0], h->mF[1], h->mV,
+                  h->mxacc, h->mroots};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->h_ctl) cudaFreeHost(h->h_ctl);
@@ -601,7 +602,7 @@ ss::Dev slimsell_graph::dev() const {
   d.fr = fr; d.par = par; d.xacc = xacc; d.xpar = xpar; d.arrive = arrive;
   d.units = units; d.units_cap = units_cap;
   d.pbest = pbest; d.psum = psum; d.touched = touched; d.mlp = mlp; d.feats = feats;
-  d.nnz = nnz; d.total_slots = slots;
+  d.nnz = nnz; d.total_slots = slots; d.reach_cap = (unsigned long long)n;
   d.ctl = ctl; d.iters = iters; d.iter_cap = iter_cap;
   return d;
 }

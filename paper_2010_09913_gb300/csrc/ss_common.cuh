@@ -84,6 +84,7 @@ struct Dev {
   const float* mlp;     // selector weights (16-64-64-4 MLP), or NULL
   float* feats;         // [iter_cap][16] selector features of each iteration of the last run
   long long nnz, total_slots;
+  unsigned long long reach_cap;  // most reached units a correct run can count (n, or n * k)
   Ctl* ctl;
   ss_iter_stats* iters; // [iter_cap]
   int iter_cap;
@@ -123,6 +124,12 @@ struct slimsell_graph {
   unsigned* touched = nullptr;
   float* mlp = nullptr;       // selector weights on the device (NULL until loaded)
   float* feats = nullptr;
+  // multi-source scratch ([n_pad][W] words), grown on demand
+  int multi_w = 0;
+  unsigned long long* mF[2] = {nullptr, nullptr};
+  unsigned long long* mV = nullptr;
+  unsigned long long* mxacc = nullptr;
+  int* mroots = nullptr;
   int smem_bytes = SS_SMEM_MAX_BYTES;  // bitmap prefix staged in shared memory
   int dp_pass = 0;                     // 1: parents by a separate DP pass after the iterations
   ss::Ctl* ctl = nullptr;

@@ -53,7 +53,7 @@ __device__ __forceinline__ void iteration_tail(const Dev& d, int variant,
   if (variant >= 0 && variant < 4) c->variant_count[variant] += 1;
   c->units = 0;
   bool stop = (nc == 0);
-  if (k >= d.n + 1 || c->reached > (unsigned long long)d.n) {
+  if (k >= d.n + 1 || c->reached > d.reach_cap) {
     c->error |= 1;
     stop = true;
   }

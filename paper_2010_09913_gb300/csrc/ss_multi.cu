@@ -1,0 +1,326 @@
+// Multi-source BFS: the boolean semiring of Section III-A run for up to 1024
+// sources at once with bit-packed frontiers (an extension beyond the paper).
+//
+//   F[k&1][r][w]  bit s of word w: row r entered source 64w+s's frontier at level k
+//   V[r][w]       visited bits (g_k = not V)
+//   x = OR over the row's neighbours u of F[u][w]; new = x & ~V; V |= new;
+//   F_next = new; dist[v][64w+s] = k for every new bit.
+//
+// One thread block handles one work item (chunk i, columns [j0, j1)); thread
+// (r, w) = threadIdx.x / W, % W owns word w of row r.  The W threads of a row
+// read the same col entry (a broadcast) and gather the W contiguous frontier
+// words of the neighbour (one W*8-byte segment).  SlimWork skips chunks whose
+// rows have every source visited; split chunks (SlimChunk) combine partial ORs
+// with 64-bit atomicOr and the last arriving block post-processes.
+#include <vector>
+
+#include "ss_device.cuh"
+
+namespace ss {
+
+struct MultiDev {
+  Dev d;
+  unsigned long long* F[2];
+  unsigned long long* V;
+  unsigned long long* xacc;  // [n_split][C][W]
+  int* dist;                 // [n][k] in original vertex order, or NULL
+  const int* roots;          // [k]
+  int k;
+};
+
+template <int C, int W, bool SLIMWORK>
+__global__ void __launch_bounds__(C * W) k_multi_pull(MultiDev m, IterLaunch il) {
+  constexpr int T = C * W;
+  const Dev& d = m.d;
+  Ctl* c = d.ctl;
+  if (c->done) return;
+  const int level = c->k;
+  const int tid = threadIdx.x, r = tid / W, w = tid % W;
+  const unsigned long long* Fp = m.F[(level - 1) & 1];
+  unsigned long long* Fn = m.F[level & 1];
+  __shared__ int s_flag;
+  unsigned long long nw = 0, deg = 0, slots = 0, act = 0;
+  unsigned maxdeg = 0;
+  for (int it = blockIdx.x; it < d.n_items; it += gridDim.x) {
+    const int4 item = d.items[it];
+    const int chunk = item.x;
+    const long long row = (long long)chunk * C + r;
+    if (SLIMWORK) {
+      const int a = d.act[chunk];
+      __syncthreads();  // every thread has read the state before it may change
+      if (a != 1) {
+        if (a >= 2 && item.y == 0) {
+          Fn[row * W + w] = 0ull;  // f_k is zero on a finished chunk
+          if (tid == 0) d.act[chunk] = (a == 3) ? 2 : 0;
+        }
+        continue;
+      }
+    }
+    const long long start = d.cs[chunk] + (long long)item.y * C;
+    const int ncol = item.z - item.y;
+    unsigned long long acc = 0ull;
+    int j = 0;
+    for (; j + 4 <= ncol; j += 4) {
+      const int c0 = __ldcs(d.col + start + (long long)(j + 0) * C + r);
+      const int c1 = __ldcs(d.col + start + (long long)(j + 1) * C + r);
+      const int c2 = __ldcs(d.col + start + (long long)(j + 2) * C + r);
+      const int c3 = __ldcs(d.col + start + (long long)(j + 3) * C + r);
+      const unsigned long long f0 = c0 >= 0 ? __ldg(Fp + (long long)c0 * W + w) : 0ull;
+      const unsigned long long f1 = c1 >= 0 ? __ldg(Fp + (long long)c1 * W + w) : 0ull;
+      const unsigned long long f2 = c2 >= 0 ? __ldg(Fp + (long long)c2 * W + w) : 0ull;
+      const unsigned long long f3 = c3 >= 0 ? __ldg(Fp + (long long)c3 * W + w) : 0ull;
+      acc |= f0 | f1 | f2 | f3;
+    }
+    for (; j < ncol; ++j) {
+      const int cc = __ldcs(d.col + start + (long long)j * C + r);
+      if (cc >= 0) acc |= __ldg(Fp + (long long)cc * W + w);
+    }
+    if (tid == 0) slots += (unsigned long long)ncol * C;
+    if (item.w >= 0) {  // SlimChunk: OR the partial rows, last block to arrive post-processes
+      unsigned long long* xa = m.xacc + ((size_t)item.w * C + r) * W + w;
+      if (acc) atomicOr(xa, acc);
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) {
+        const unsigned old = atomicAdd(d.arrive + item.w, 1u);
+        s_flag = (old == (unsigned)d.split_n[item.w] - 1u);
+      }
+      __syncthreads();
+      if (!s_flag) continue;
+      __threadfence();
+      acc = __ldcg(xa);
+      *xa = 0ull;
+      if (tid == 0) d.arrive[item.w] = 0u;
+    }
+    const unsigned long long vold = m.V[row * W + w];
+    const unsigned long long nb = acc & ~vold;
+    if (nb) {
+      m.V[row * W + w] = vold | nb;
+      const int pc = __popcll(nb);
+      const int dv = d.rdeg[row];
+      nw += (unsigned long long)pc;
+      deg += (unsigned long long)pc * (unsigned long long)dv;
+      maxdeg = max(maxdeg, (unsigned)dv);
+      if (m.dist) {
+        int* out = m.dist + (long long)d.perm[row] * m.k + 64 * w;
+        unsigned long long b = nb;
+        while (b) {
+          const int s = __ffsll((long long)b) - 1;
+          b &= b - 1;
+          out[s] = level;
+        }
+      }
+    }
+    Fn[row * W + w] = nb;
+    const int left = __syncthreads_or((vold | nb) != ~0ull);
+    if (tid == 0) {
+      d.act[chunk] = left ? 1 : 3;
+      act += 1;
+    }
+  }
+  finish_iteration_block<T>(d, nw, deg, slots, act, maxdeg, il);
+}
+
+__global__ void k_multi_init(MultiDev m, int W) {
+  const Dev& d = m.d;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long words = (long long)d.n_pad * W;
+  // padding rows and sources beyond k count as visited
+  for (long long i = t0; i < words; i += stride) {
+    const long long r = i / W;
+    const int w = (int)(i % W);
+    unsigned long long v = 0ull;
+    if (r >= d.n) {
+      v = ~0ull;
+    } else {
+      const int lo = 64 * w;  // sources lo .. lo+63; those >= k never exist
+      if (lo >= m.k) v = ~0ull;
+      else if (m.k - lo < 64) v = ~0ull << (m.k - lo);
+    }
+    m.V[i] = v;
+    m.F[0][i] = 0ull;
+    m.F[1][i] = 0ull;
+  }
+  for (long long i = t0; i < d.n_c; i += stride) d.act[i] = 1;
+  for (long long s = t0; s < (long long)d.n_split * d.C * W; s += stride) m.xacc[s] = 0ull;
+}
+
+__global__ void k_multi_roots(MultiDev m, int W) {
+  const Dev& d = m.d;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < m.k; s += gridDim.x * blockDim.x) {
+    const int v = m.roots[s];
+    const long long r = d.invperm[v];
+    const unsigned long long bit = 1ull << (s & 63);
+    atomicOr(m.V + r * W + s / 64, bit);
+    atomicOr(m.F[0] + r * W + s / 64, bit);
+    if (m.dist) m.dist[(long long)v * m.k + s] = 0;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    Ctl* c = d.ctl;
+    unsigned long long rd = 0;
+    for (int s = 0; s < m.k; ++s) rd += (unsigned long long)d.rdeg[d.invperm[m.roots[s]]];
+    c->k = 1; c->done = 0; c->error = 0; c->variant = -1;
+    c->new_count = 0; c->new_deg = 0; c->slots = 0; c->active = 0;
+    c->reached = (unsigned long long)m.k; c->reached_deg = rd;
+    c->total_slots = 0; c->dp_slots = 0; c->blocks_done = 0;
+    c->prev_variant = -1; c->prev_slots = 0; c->prev_new = (unsigned long long)m.k; c->prev_deg = rd;
+    c->prev2_new = 0; c->prev_active = 0; c->new_maxdeg = 0; c->prev_maxdeg = 0; c->units = 0;
+    c->loop_guard = 0;
+    for (int v = 0; v < 4; ++v) c->variant_count[v] = 0;
+    ss_iter_stats st;
+    st.frontier = m.k; st.frontier_degree = (long long)rd; st.slots = 0; st.active_chunks = 0;
+    st.variant = -1; st.kernel_ns = 0;
+    d.iters[0] = st;
+  }
+}
+
+template <int C, int W>
+static ss_status launch_multi_cw(const slimsell_graph* h, const MultiDev& m, bool slimwork,
+                                 const IterLaunch& il, cudaStream_t st) {
+  if constexpr (C * W < 32) {
+    set_error("slimsell_bfs_multi: C * ceil(k / 64) must be at least 32");
+    return SS_ERR_UNSUPPORTED;
+  } else {
+    static int grid[2] = {0, 0};
+    int& g = grid[slimwork ? 1 : 0];
+    if (!g) {
+      int b = 0;
+      if (slimwork) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_multi_pull<C, W, true>, C * W, 0);
+      else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_multi_pull<C, W, false>, C * W, 0);
+      g = (b > 0 ? b : 1) * h->num_sms;
+    }
+    if (slimwork) k_multi_pull<C, W, true><<<g, C * W, 0, st>>>(m, il);
+    else k_multi_pull<C, W, false><<<g, C * W, 0, st>>>(m, il);
+    SS_CUDA(cudaGetLastError());
+    return SS_OK;
+  }
+}
+
+template <int C>
+static ss_status launch_multi_c(const slimsell_graph* h, const MultiDev& m, int W, bool slimwork,
+                                const IterLaunch& il, cudaStream_t st) {
+  switch (W) {
+    case 1: return launch_multi_cw<C, 1>(h, m, slimwork, il, st);
+    case 2: return launch_multi_cw<C, 2>(h, m, slimwork, il, st);
+    case 4: return launch_multi_cw<C, 4>(h, m, slimwork, il, st);
+    case 8: return launch_multi_cw<C, 8>(h, m, slimwork, il, st);
+    default: return launch_multi_cw<C, 16>(h, m, slimwork, il, st);
+  }
+}
+
+static ss_status launch_multi(const slimsell_graph* h, const MultiDev& m, int W, bool slimwork,
+                              const IterLaunch& il, cudaStream_t st) {
+  switch (h->C) {
+    case 8: return launch_multi_c<8>(h, m, W, slimwork, il, st);
+    case 16: return launch_multi_c<16>(h, m, W, slimwork, il, st);
+    case 32: return launch_multi_c<32>(h, m, W, slimwork, il, st);
+    default: return launch_multi_c<64>(h, m, W, slimwork, il, st);
+  }
+}
+
+// Multi-source scratch, grown on demand and kept with the handle.
+static ss_status ensure_multi_scratch(slimsell_graph* h, int W) {
+  if (h->multi_w >= W) return SS_OK;
+  void* ptrs[] = {h->mF[0], h->mF[1], h->mV, h->mxacc, h->mroots};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  h->mF[0] = h->mF[1] = h->mV = h->mxacc = nullptr;
+  h->mroots = nullptr;
+  h->multi_w = 0;
+  const size_t words = (size_t)h->n_pad * W;
+  ss_status s;
+  for (int b = 0; b < 2; ++b)
+    if ((s = dmalloc(h, (void**)&h->mF[b], sizeof(unsigned long long) * words)) != SS_OK) return s;
+  if ((s = dmalloc(h, (void**)&h->mV, sizeof(unsigned long long) * words)) != SS_OK) return s;
+  const size_t ns = (size_t)(h->n_split > 0 ? h->n_split : 1) * h->C * W;
+  if ((s = dmalloc(h, (void**)&h->mxacc, sizeof(unsigned long long) * ns)) != SS_OK) return s;
+  if ((s = dmalloc(h, (void**)&h->mroots, sizeof(int) * 1024)) != SS_OK) return s;
+  h->multi_w = W;
+  return SS_OK;
+}
+
+}  // namespace ss
+
+extern "C" ss_status slimsell_bfs_multi(slimsell_handle h, const int32_t* d_roots, int32_t k,
+                                        int32_t policy, int32_t* d_dist, void* stream) {
+  using namespace ss;
+  set_error("");
+  if (!h || !d_roots) {
+    set_error("slimsell_bfs_multi: NULL argument");
+    return SS_ERR_INVALID;
+  }
+  if (k < 1 || k > 1024) {
+    set_error("slimsell_bfs_multi: k must be in [1, 1024] (got %d)", k);
+    return SS_ERR_INVALID;
+  }
+  if (policy != SS_V_FULL && policy != SS_V_SLIMWORK) {
+    set_error("slimsell_bfs_multi: policy must be SS_V_FULL or SS_V_SLIMWORK");
+    return SS_ERR_INVALID;
+  }
+  int W = 1;
+  while (64 * W < k) W *= 2;
+  while (h->C * W < 32) W *= 2;  // a block needs a full warp; extra words hold no source
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<int> roots((size_t)k);
+  SS_CUDA(cudaMemcpyAsync(roots.data(), d_roots, sizeof(int) * (size_t)k, cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaStreamSynchronize(st));
+  for (int s = 0; s < k; ++s)
+    if (roots[(size_t)s] < 0 || roots[(size_t)s] >= h->n) {
+      set_error("slimsell_bfs_multi: root %d of source %d out of range", roots[(size_t)s], s);
+      return SS_ERR_INVALID;
+    }
+  if (h->pending) SS_CUDA(cudaEventSynchronize(h->ev_done));
+  h->pending = 0;
+  ss_status s = ensure_multi_scratch(h, W);
+  if (s != SS_OK) return s;
+  SS_CUDA(cudaMemcpyAsync(h->mroots, d_roots, sizeof(int) * (size_t)k, cudaMemcpyDeviceToDevice, st));
+  MultiDev m;
+  m.d = h->dev();
+  m.d.reach_cap = (unsigned long long)h->n * (unsigned long long)k;
+  m.F[0] = h->mF[0];
+  m.F[1] = h->mF[1];
+  m.V = h->mV;
+  m.xacc = h->mxacc;
+  m.dist = d_dist;
+  m.roots = h->mroots;
+  m.k = k;
+  const bool prof = h->profiling != 0;
+  h->iter_ns.clear();
+  double iter_ms = 0.0;
+  if (prof) SS_CUDA(cudaEventRecord(h->ev_c, st));
+  if (d_dist) SS_CUDA(cudaMemsetAsync(d_dist, 0xff, sizeof(int) * (size_t)h->n * (size_t)k, st));
+  k_multi_init<<<8 * h->num_sms, 256, 0, st>>>(m, W);
+  k_multi_roots<<<(k + 255) / 256, 256, 0, st>>>(m, W);
+  SS_CUDA(cudaGetLastError());
+  const IterLaunch il{policy, 0, 0};
+  const long long max_iter = (long long)h->n + 2;
+  for (long long it = 0;; ++it) {
+    if (it > max_iter) {
+      set_error("slimsell_bfs_multi: no convergence after %lld iterations", it);
+      return SS_ERR_CUDA;
+    }
+    if (prof) SS_CUDA(cudaEventRecord(h->ev_a, st));
+    s = launch_multi(h, m, W, policy == SS_V_SLIMWORK, il, st);
+    if (s != SS_OK) return s;
+    if (prof) SS_CUDA(cudaEventRecord(h->ev_b, st));
+    SS_CUDA(cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    SS_CUDA(cudaStreamSynchronize(st));
+    if (prof) {
+      float ms = 0.f;
+      SS_CUDA(cudaEventElapsedTime(&ms, h->ev_a, h->ev_b));
+      iter_ms += ms;
+      h->iter_ns.push_back((int)(ms * 1.0e6f));
+    }
+    if (h->h_ctl->done) break;
+  }
+  if (prof) SS_CUDA(cudaEventRecord(h->ev_d, st));
+  SS_CUDA(cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaEventRecord(h->ev_done, st));
+  h->last.semiring = SS_BOOLEAN;
+  h->last.iter_kernel_ms = iter_ms;
+  h->last.total_ms = 0.0;
+  h->pending = 1;
+  ss_run_stats tmp;
+  return slimsell_get_run_stats(h, &tmp, nullptr, 0);
+}
