@@ -145,3 +145,35 @@ def test_training_reduces_loss():
             torch.cuda.synchronize()
             losses.append(loss.item())
     assert losses[1] < 0.1 * losses[0], losses
+
+
+def test_selector_training_pipeline():
+    """Collect per-iteration variant timings, train the MLP on the GPU, and check what it
+    learned: its argmin matches the measured-fastest variant on most iterations, and the
+    learned schedule costs no more than the slower fixed schedules."""
+    from paper_2010_09913_gb300 import selector
+
+    graphs = [gg.kronecker(15, seed=3), gg.lattice(96, 0.05, seed=2)]
+    Xs, Ts, Ms, handles = [], [], [], []
+    for g in graphs:
+        G = ss.SlimSellGraph.from_host(g.row_ptr, g.col, C=32, sigma=g.n, split_w=256)
+        X, T, M = selector.collect(G, gg.roots(g, 2, seed=4), "tropical", repeats=2)
+        Xs.append(X); Ts.append(T); Ms.append(M); handles.append((G, g))
+    X, T, M = np.concatenate(Xs), np.concatenate(Ts), np.concatenate(Ms)
+    assert X.shape[1] == 16 and np.all(M.sum(1) == 4)  # every variant ran every iteration
+    w, loss = selector.train(X, T, M, steps=2500, lr=3e-3, seed=1)
+    assert np.isfinite(loss) and loss < 0.5 * float(np.var(T))
+    y = torch.empty((X.shape[0], 4), device="cuda")
+    ss.slimsell_mlp_forward(torch.from_numpy(w).cuda(), torch.from_numpy(X).cuda(), y)
+    torch.cuda.synchronize()
+    pred = y.cpu().numpy().argmin(1)
+    best = T.argmin(1)
+    # near-ties (within 10%) count as a match
+    close = T[np.arange(len(pred)), pred] <= T[np.arange(len(best)), best] + np.log(1.10)
+    assert close.mean() >= 0.6, close.mean()
+    G, g = handles[0]
+    res = selector.evaluate(G, gg.roots(g, 2, seed=4), "tropical", weights=w, repeats=2)
+    worst_fixed = max(res[v] for v in selector.VARIANTS)
+    assert res["learned"] <= worst_fixed, res
+    for G, _ in handles:
+        G.close()
