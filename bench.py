@@ -222,6 +222,116 @@ def workload_config(args, g):
             "outputs": "int32 dist + parent per run (DP for tropical/real/boolean)"}
 
 
+def time_policy(ss, torch, h, roots, policy, stream, runs_edges):
+    """Device-side loops, CUDA events around every run of every semiring."""
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for sr in SEMIRINGS:
+        for r in roots:
+            ss.slimsell_bfs(h, int(r), SR_ID[sr], policy, None, None, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return runs_edges / (ms / 1000.0) / 1e9, ms
+
+
+def batched_learned(ss, torch, g, h, roots, args, stream, dev, runs_edges):
+    """On the same graph: heuristic and learned per-iteration schedules of
+    single-source BFS, and bit-packed multi-source batches."""
+    from paper_2010_09913_gb300 import selector
+    out = {"unit": "GTEPS", "graph": f"kronecker scale {args.scale}"}
+    gte, _ = time_policy(ss, torch, h, roots, ss.V_SLIMWORK, stream, runs_edges)
+    out["plain_slimwork_single"] = gte
+    gte, _ = time_policy(ss, torch, h, roots, ss.V_HEURISTIC, stream, runs_edges)
+    out["heuristic_single"] = gte
+    # train the selector on other (smaller) generated graphs, evaluate on this one
+    t0 = time.perf_counter()
+    Xs, Ts, Ms = [], [], []
+    for tg in (gg.kronecker(16, seed=7), gg.lattice(256, 0.05, seed=7), gg.erdos_renyi(1 << 16, 16.0, seed=7)):
+        G = ss.SlimSellGraph.from_host(tg.row_ptr, tg.col, C=32, sigma=tg.n, split_w=args.split_w)
+        X, T, M = selector.collect(G, gg.roots(tg, 3, seed=8), "tropical", repeats=2)
+        Xs.append(X); Ts.append(T); Ms.append(M)
+        G.close()
+    w, loss = selector.train(np.concatenate(Xs), np.concatenate(Ts), np.concatenate(Ms), steps=3000)
+    out["selector_training"] = {"samples": int(sum(x.shape[0] for x in Xs)), "final_loss": loss,
+                                "seconds": time.perf_counter() - t0,
+                                "graphs": "kronecker 16, lattice 256^2 (5% deleted), ER 2^16 (mean deg 16)"}
+    ss.slimsell_selector_load(h, w)
+    for sr in SEMIRINGS:  # build the learned loop graphs outside the timed region
+        ss.slimsell_bfs(h, int(roots[0]), SR_ID[sr], ss.V_LEARNED, None, None, stream)
+    gte, _ = time_policy(ss, torch, h, roots, ss.V_LEARNED, stream, runs_edges)
+    out["learned_single"] = gte
+    ev = selector.evaluate(ss.SlimSellGraph.wrap(h, g.n), roots[:4], "tropical", weights=w, repeats=2)
+    out["schedule_kernel_ms_tropical_4roots"] = {k: round(v, 4) for k, v in ev.items()}
+    # multi-source batches on the same graph
+    for k in (64, 256, 1024):
+        mroots = gg.roots(g, k, seed=20 + k)
+        r_d = torch.from_numpy(mroots).to(dev)
+        dist = torch.empty((g.n, k), dtype=torch.int32, device=dev)
+        ss.slimsell_bfs_multi(h, r_d, ss.V_SLIMWORK, dist, stream)  # warm
+        st, _ = ss.slimsell_get_run_stats(h)
+        edges = st.reached_degree // 2
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        reps = 2
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            ss.slimsell_bfs_multi(h, r_d, ss.V_SLIMWORK, dist, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[f"multi_{k}"] = edges / (ms / 1000.0) / 1e9
+        out[f"multi_{k}_ms"] = ms
+        del dist
+    ss.slimsell_selector_load(h, None)
+    best_single = max(out["heuristic_single"], out["learned_single"])
+    out["best_batched_or_learned_over_plain"] = max(best_single, out["multi_1024"]) / out["plain_slimwork_single"]
+    return out
+
+
+def roofline_at_scale(ss, torch, scale, nroots, split_w, stream, dev):
+    """Plain single-source SlimSell BFS (SlimWork + SlimChunk) at a larger scale:
+    iteration-kernel GB/s from per-launch CUDA events, and whole-run GTEPS."""
+    g = gg.kronecker(scale, seed=1)
+    roots = gg.roots(g, nroots, seed=2)
+    rp_d = torch.from_numpy(g.row_ptr).to(dev)
+    col_d = torch.from_numpy(g.col).to(dev)
+    h = ss.slimsell_build(rp_d, col_d, g.n, g.nnz, 32, g.n, split_w, stream)
+    del rp_d, col_d
+    hbm, kind = load_peaks()
+    out = {"graph": f"kronecker scale {scale}", "n": g.n, "nnz": g.nnz, "roots": nroots}
+    for sr in ("tropical", "boolean"):
+        ss.slimsell_set_profiling(h, True)
+        bytes_, ms_, edges = 0.0, 0.0, 0
+        for r in roots:
+            ss.slimsell_bfs(h, int(r), SR_ID[sr], ss.V_SLIMWORK, None, None, stream)
+            st, its = ss.slimsell_get_run_stats(h, cap=4096)
+            for i in range(1, st.iterations + 1):
+                bytes_ += iteration_bytes(its[i], sr, g.n, 32)
+            ms_ += st.iter_kernel_ms
+            edges += st.reached_degree // 2
+        ss.slimsell_set_profiling(h, False)
+        ach = bytes_ / (ms_ / 1000.0) / 1e9
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for r in roots:
+            ss.slimsell_bfs(h, int(r), SR_ID[sr], ss.V_SLIMWORK, None, None, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[sr] = {"iteration_kernel_gbs": ach, "hbm_frac": ach / hbm, "peak": hbm, "peak_kind": kind,
+                   "gteps_slimwork": edges / (ms / 1000.0) / 1e9}
+        gte, _ = time_policy(ss, torch, h, roots, ss.V_HEURISTIC, stream, 4 * edges)
+        out[sr]["gteps_heuristic_all4"] = gte
+    ss.slimsell_destroy(h)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -234,6 +344,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ablations", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-scale24", action="store_true")
     args = ap.parse_args()
     world, rank, local, pg = dist_setup()
     if args.impl == "reference":
@@ -357,11 +469,18 @@ def main():
             "layout": {"slots": info.slots, "padding": info.padding, "n_items": info.n_items,
                        "n_split_chunks": info.n_split_chunks, "max_degree": info.max_degree}}
 
+    if not args.no_batched and rank == 0:
+        line["batched_learned"] = batched_learned(ss, torch, g, h, roots, args, stream, dev,
+                                                  edges_per_step)
     if not args.no_e2e:
         line["e2e"] = e2e_measure(ss, torch, g, roots, args, stream, dev, pg)
     if not args.no_ablations and rank == 0:
         line["ablations"] = ablations(ss, torch, g, roots[:8], h, rp_d, col_d, args, stream, dev)
     ss.slimsell_destroy(h)
+    del rp_d, col_d
+    if not args.no_scale24 and rank == 0:
+        torch.cuda.empty_cache()
+        line["scale24"] = roofline_at_scale(ss, torch, 24, 8, args.split_w, stream, dev)
     if rank == 0 and world == 1 and not args.no_cpu:
         edges, t_cpu, nruns = cpu_oracle_sample(g, roots, 20.0)
         line["cpu_baseline"] = {"value": edges / t_cpu / 1e9, "unit": "GTEPS", "cores": 1,

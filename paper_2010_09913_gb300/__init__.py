@@ -246,6 +246,13 @@ class SlimSellGraph:
                                 split_w, stream)
 
     @classmethod
+    def wrap(cls, h: int, n: int):
+        """View an existing handle (not owned: close() leaves it alone)."""
+        obj = cls.__new__(cls)
+        obj.h, obj.n, obj._owned = h, n, False
+        return obj
+
+    @classmethod
     def from_host(cls, row_ptr, col, device="cuda", **kw):
         rp = torch.as_tensor(row_ptr, dtype=torch.int64).to(device)
         c = torch.as_tensor(col, dtype=torch.int32).to(device)
@@ -297,9 +304,9 @@ class SlimSellGraph:
                 "items": items[: inf.n_items * 4].view(-1, 4)}
 
     def close(self):
-        if getattr(self, "h", None):
+        if getattr(self, "h", None) and getattr(self, "_owned", True):
             slimsell_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:
