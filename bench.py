@@ -38,15 +38,19 @@ FRONTIER_BYTES = {"tropical": 4.0, "real": 4.0, "boolean": 0.125, "selmax": 4.0}
 FRONTIER_WRITE = {"tropical": 0.0, "real": 4.0, "boolean": 0.125, "selmax": 4.0}
 
 # DRAM traffic per k_pull launch measured by ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum) on this workload, keyed by the hash of the kernel source
-# it was taken on; reported as null once the source changes.
-NCU_TRAFFIC = {}
+# dram__bytes_write.sum, mean over the 56 tropical iterations of the first 8 roots
+# of this workload; profiles/k_pull_kron22.md), keyed by the hash of the kernel
+# sources it was taken on; reported as null once those sources change.
+NCU_TRAFFIC = {"7cf2bf4c7ed4681d": 237.9e6}
+KERNEL_SOURCES = ["ss_bfs.cu", "ss_device.cuh", "ss_common.cuh"]
 
 
 def kernel_source_hash() -> str:
-    p = os.path.join(ROOT, "paper_2010_09913_gb300", "csrc", "ss_bfs.cu")
-    with open(p, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2010_09913_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def load_peaks():
