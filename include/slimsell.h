@@ -34,6 +34,7 @@ extern "C" {
 #endif
 
 typedef struct slimsell_graph* slimsell_handle;
+typedef struct slimsell_batch* slimsell_batch_handle;
 
 /* Semirings of Section III-A. */
 typedef enum {
@@ -156,6 +157,29 @@ ss_status slimsell_bfs(slimsell_handle h, int32_t root, int32_t semiring, int32_
  */
 ss_status slimsell_bfs_multi(slimsell_handle h, const int32_t* d_roots, int32_t k, int32_t policy,
                              int32_t* d_dist, void* stream);
+
+/*
+ * Batched BFS over many graphs (an extension beyond the paper): one executable
+ * CUDA graph holding, per handle, the chain init -> root -> device-side
+ * iteration loop -> output, so that one launch runs every BFS and the chains
+ * overlap on the GPU.
+ *   slimsell_batch_create: hs = g distinct handles on the current device,
+ *     semiring / policy as for slimsell_bfs (applied to every graph).  The
+ *     handles stay owned by the caller and must outlive the batch; while a batch
+ *     run is in flight they must not be used by other calls.
+ *   slimsell_batch_run: d_roots int32[g] device (root of graph i, checked);
+ *     h_dist / h_parent: host arrays of g device pointers (int32[n_i] each, an
+ *     entry or the whole array may be NULL).  Stream-ordered, returns once queued.
+ *   slimsell_batch_get_stats: waits for the last run; out[g] (host) receives
+ *     each graph's iterations, reached vertices and reached degree sum.
+ * Errors: SS_ERR_INVALID, SS_ERR_OOM, SS_ERR_CUDA.
+ */
+ss_status slimsell_batch_create(const slimsell_handle* hs, int32_t g, int32_t semiring,
+                                int32_t policy, slimsell_batch_handle* out);
+ss_status slimsell_batch_run(slimsell_batch_handle b, const int32_t* d_roots,
+                             int32_t* const* h_dist, int32_t* const* h_parent, void* stream);
+ss_status slimsell_batch_get_stats(slimsell_batch_handle b, ss_run_stats* out);
+void slimsell_batch_destroy(slimsell_batch_handle b);
 
 /* Layout summary. */
 ss_status slimsell_get_info(slimsell_handle h, ss_info* out);

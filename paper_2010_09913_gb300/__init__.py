@@ -81,6 +81,10 @@ def lib():
         "slimsell_mlp_forward": (i32, [_VP, _VP, i32, _VP, _VP]),
         "slimsell_mlp_train_step": (i32, [_VP, _VP, _VP, i32, _VP, _VP, _VP, i32, ctypes.c_float,
                                           _VP, _VP, _VP]),
+        "slimsell_batch_create": (i32, [_VP, i32, i32, i32, ctypes.POINTER(_VP)]),
+        "slimsell_batch_run": (i32, [_VP, _VP, _VP, _VP, _VP]),
+        "slimsell_batch_get_stats": (i32, [_VP, ctypes.POINTER(ss_run_stats)]),
+        "slimsell_batch_destroy": (None, [_VP]),
         "slimsell_last_error": (ctypes.c_char_p, []),
         "slimsell_version": (ctypes.c_char_p, []),
     }
@@ -97,7 +101,8 @@ def exported_symbols() -> list[str]:
             "slimsell_set_profiling", "slimsell_set_option", "slimsell_export_layout",
             "slimsell_destroy",
             "slimsell_sigma_sort_noalloc", "slimsell_selector_load", "slimsell_get_features",
-            "slimsell_mlp_forward", "slimsell_mlp_train_step",
+            "slimsell_mlp_forward", "slimsell_mlp_train_step", "slimsell_batch_create",
+            "slimsell_batch_run", "slimsell_batch_get_stats", "slimsell_batch_destroy",
             "slimsell_last_error", "slimsell_version"]
 
 
@@ -218,6 +223,35 @@ def slimsell_mlp_train_step(w, m, v, step, x, t, mask, lr, grad=None, loss=None,
         _ptr(x, torch.float32, "x"), _ptr(t, torch.float32, "t"), _ptr(mask, torch.float32, "mask"),
         int(x.shape[0]), float(lr), _ptr(grad, torch.float32, "grad") if grad is not None else None,
         _ptr(loss, torch.float32, "loss") if loss is not None else None, _stream(stream)))
+
+
+def slimsell_batch_create(handles, semiring: int, policy: int) -> int:
+    arr = (_VP * len(handles))(*handles)
+    b = _VP()
+    _check("slimsell_batch_create", lib().slimsell_batch_create(
+        arr, len(handles), int(semiring), int(policy), ctypes.byref(b)))
+    return b.value
+
+
+def slimsell_batch_run(b: int, roots: torch.Tensor, dists=None, parents=None, stream=None) -> None:
+    """roots: int32 CUDA tensor [g]; dists / parents: lists of int32 CUDA tensors (or None)."""
+    def ptrs(ts):
+        if ts is None:
+            return None
+        return (_VP * len(ts))(*[(_ptr(t, torch.int32, "output") if t is not None else None) for t in ts])
+    _check("slimsell_batch_run", lib().slimsell_batch_run(
+        b, _ptr(roots, torch.int32, "roots"), ptrs(dists), ptrs(parents), _stream(stream)))
+
+
+def slimsell_batch_get_stats(b: int, g: int):
+    out = (ss_run_stats * g)()
+    _check("slimsell_batch_get_stats", lib().slimsell_batch_get_stats(b, out))
+    return list(out)
+
+
+def slimsell_batch_destroy(b: int) -> None:
+    if b:
+        lib().slimsell_batch_destroy(b)
 
 
 def slimsell_destroy(h: int) -> None:

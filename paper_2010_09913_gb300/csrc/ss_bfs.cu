@@ -32,6 +32,8 @@
 // lane l always meets rows 4*(l mod C/4) .. +3; lanes sharing rows are combined
 // with xor-shuffles.  Split chunks (SlimChunk) combine partial rows with
 // atomics; the last item of a chunk to arrive runs the post-processing.
+#include <algorithm>
+
 #include "ss_device.cuh"
 
 namespace ss {
@@ -382,27 +384,7 @@ __global__ void k_init(Dev d) {
   }
 }
 
-__global__ void k_init_root(Dev d, int root) {
-  const int r = d.invperm[root];
-  d.lvl[r] = 0;
-  d.fb[0][r >> 5] |= 1u << (r & 31);
-  d.fr[r] = 1.0f;
-  d.par[r] = root + 1;
-  Ctl* c = d.ctl;
-  c->k = 1; c->done = 0; c->error = 0; c->variant = -1;
-  c->new_count = 0; c->new_deg = 0; c->slots = 0; c->active = 0;
-  c->reached = 1; c->reached_deg = (unsigned long long)d.rdeg[r];
-  c->total_slots = 0; c->dp_slots = 0; c->blocks_done = 0;
-  c->prev_variant = -1; c->prev_slots = 0; c->prev_new = 1; c->prev_deg = (unsigned long long)d.rdeg[r];
-  c->prev2_new = 0; c->prev_active = 0; c->new_maxdeg = 0; c->prev_maxdeg = (unsigned)d.rdeg[r];
-  c->units = 0;
-  for (int v = 0; v < 4; ++v) c->variant_count[v] = 0;
-  c->loop_guard = 0;
-  ss_iter_stats s;
-  s.frontier = 1; s.frontier_degree = d.rdeg[r]; s.slots = 0; s.active_chunks = 0;
-  s.variant = -1; s.kernel_ns = 0;
-  d.iters[0] = s;
-}
+__global__ void k_init_root(Dev d, int root) { init_root_state(d, root); }
 
 // DP transformation as a separate pass (Section II-C): the parent of a row at
 // level L >= 1 is its largest-id neighbour at level L-1.  Neighbours are stored
@@ -514,19 +496,23 @@ __global__ void k_dp_clear(Dev d) {
   }
 }
 
-__global__ void k_output(Dev d, int* dist, int* parent) {
-  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < d.n;
-       v += (long long)gridDim.x * blockDim.x) {
-    const int r = d.invperm[v];
-    const int L = d.lvl[r];
-    if (dist) dist[v] = (L == SS_INF) ? -1 : L;
-    if (parent) parent[v] = (L == SS_INF) ? -1 : d.par[r] - 1;
-  }
-}
+__global__ void k_output(Dev d, int* dist, int* parent) { write_outputs(d, dist, parent); }
 
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
+// One 1024-thread block per SM, fewer for small work lists (about 128 items
+// per block), so that several small graphs can share the GPU.
+int pull_grid(const slimsell_graph* h) {
+  const long long want = ((long long)h->n_items + 127) / 128;
+  return (int)std::max(1LL, std::min((long long)h->num_sms, want));
+}
+
+int vertex_grid(const slimsell_graph* h, int threads) {
+  const long long want = ((long long)h->n_pad + threads - 1) / threads;
+  return (int)std::max(1LL, std::min((long long)8 * h->num_sms, want));
+}
+
 template <int SR, int C, int MODE>
 static ss_status launch_pull(const slimsell_graph* h, const Dev& d, const IterLaunch& il,
                              cudaStream_t st) {
@@ -536,7 +522,7 @@ static ss_status launch_pull(const slimsell_graph* h, const Dev& d, const IterLa
                                  SS_SMEM_LIMIT_BYTES));
     configured = true;
   }
-  k_pull<SR, C, MODE><<<h->num_sms, PULL_THREADS, (size_t)(d.smem_words + SMEM_GUARD) * 4, st>>>(
+  k_pull<SR, C, MODE><<<pull_grid(h), PULL_THREADS, (size_t)(d.smem_words + SMEM_GUARD) * 4, st>>>(
       d, il.variant, il.cond, il.use_cond);
   SS_CUDA(cudaGetLastError());
   return SS_OK;
@@ -614,6 +600,46 @@ static ss_status capture_into(slimsell_graph* h, const Dev& d, int sr, int varia
 // followed by a SWITCH node over the four variants.  The last block of each
 // iteration's final kernel sets the WHILE condition.  Built once per
 // (semiring, policy, staged-prefix size) and cached in the handle.
+// Add one device-side iteration loop to graph g after the given dependencies:
+// a conditional WHILE node whose body is the fixed variant's kernels, or (adaptive
+// policies) the decide kernel followed by a conditional SWITCH over the four
+// variants.  The last block of each iteration's final kernel sets the WHILE
+// condition.
+ss_status add_loop_node(slimsell_graph* h, const Dev& d, int sr, int policy, cudaGraph_t g,
+                        const cudaGraphNode_t* deps, size_t ndeps, cudaGraphNode_t* out) {
+  cudaGraphConditionalHandle cw;
+  cudaGraphNodeParams wp = {};
+  cudaError_t e = cudaGraphConditionalHandleCreate(&cw, g, 1, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) {
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = cw;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    e = cudaGraphAddNode(out, g, deps, nullptr, ndeps, &wp);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "conditional WHILE node");
+  cudaGraph_t body = wp.conditional.phGraph_out[0];
+  if (!adaptive(policy)) return capture_into(h, d, sr, policy, IterLaunch{policy, cw, 1}, body);
+  cudaGraphConditionalHandle csw;
+  cudaGraphNode_t dnode, snode;
+  cudaGraphNodeParams sp = {};
+  e = cudaGraphConditionalHandleCreate(&csw, body, 0, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphConditionalHandleCreate(switch)");
+  ss_status s = add_decide_node(h, d, policy, csw, cw, body, &dnode);
+  if (s != SS_OK) return s;
+  sp.type = cudaGraphNodeTypeConditional;
+  sp.conditional.handle = csw;
+  sp.conditional.type = cudaGraphCondTypeSwitch;
+  sp.conditional.size = 4;
+  e = cudaGraphAddNode(&snode, body, &dnode, nullptr, 1, &sp);
+  if (e != cudaSuccess) return cuda_fail(e, "conditional SWITCH node");
+  for (int v = 0; v < 4 && s == SS_OK; ++v)
+    s = capture_into(h, d, sr, v, IterLaunch{v, cw, 1}, sp.conditional.phGraph_out[v]);
+  return s;
+}
+
+// The single-call loop graph, built once per (semiring, policy, staged-prefix
+// size) and cached in the handle.
 static ss_status loop_graph(slimsell_graph* h, const Dev& d, int sr, int policy,
                             cudaGraphExec_t* out) {
   cudaGraphExec_t& slot = h->loop_exec[sr][policy];
@@ -627,45 +653,10 @@ static ss_status loop_graph(slimsell_graph* h, const Dev& d, int sr, int policy,
   }
   cudaGraph_t g = nullptr;
   SS_CUDA(cudaGraphCreate(&g, 0));
-  ss_status s = SS_OK;
-  cudaError_t e;
-  cudaGraphConditionalHandle cw;
-  cudaGraphNodeParams wp = {};
   cudaGraphNode_t wnode;
-  e = cudaGraphConditionalHandleCreate(&cw, g, 1, cudaGraphCondAssignDefault);
-  if (e == cudaSuccess) {
-    wp.type = cudaGraphNodeTypeConditional;
-    wp.conditional.handle = cw;
-    wp.conditional.type = cudaGraphCondTypeWhile;
-    wp.conditional.size = 1;
-    e = cudaGraphAddNode(&wnode, g, nullptr, nullptr, 0, &wp);
-  }
-  if (e != cudaSuccess) s = cuda_fail(e, "conditional WHILE node");
+  ss_status s = add_loop_node(h, d, sr, policy, g, nullptr, 0, &wnode);
   if (s == SS_OK) {
-    cudaGraph_t body = wp.conditional.phGraph_out[0];
-    if (!adaptive(policy)) {
-      s = capture_into(h, d, sr, policy, IterLaunch{policy, cw, 1}, body);
-    } else {
-      cudaGraphConditionalHandle csw;
-      cudaGraphNode_t dnode, snode;
-      cudaGraphNodeParams sp = {};
-      e = cudaGraphConditionalHandleCreate(&csw, body, 0, 0);
-      if (e != cudaSuccess) s = cuda_fail(e, "cudaGraphConditionalHandleCreate(switch)");
-      if (s == SS_OK) s = add_decide_node(h, d, policy, csw, cw, body, &dnode);
-      if (s == SS_OK) {
-        sp.type = cudaGraphNodeTypeConditional;
-        sp.conditional.handle = csw;
-        sp.conditional.type = cudaGraphCondTypeSwitch;
-        sp.conditional.size = 4;
-        e = cudaGraphAddNode(&snode, body, &dnode, nullptr, 1, &sp);
-        if (e != cudaSuccess) s = cuda_fail(e, "conditional SWITCH node");
-      }
-      for (int v = 0; v < 4 && s == SS_OK; ++v)
-        s = capture_into(h, d, sr, v, IterLaunch{v, cw, 1}, sp.conditional.phGraph_out[v]);
-    }
-  }
-  if (s == SS_OK) {
-    e = cudaGraphInstantiate(&slot, g, 0);
+    cudaError_t e = cudaGraphInstantiate(&slot, g, 0);
     if (e != cudaSuccess) {
       slot = nullptr;
       s = cuda_fail(e, "cudaGraphInstantiate");
@@ -747,7 +738,7 @@ ss_status slimsell_bfs(slimsell_handle h, int32_t root, int32_t semiring, int32_
   }
   cudaStream_t st = (cudaStream_t)stream;
   const Dev d = h->dev();
-  const int grid = 8 * h->num_sms;
+  const int grid = vertex_grid(h, 256);
   const bool prof = h->profiling != 0;
   const bool device_loop = h->device_loop && !prof;
   if (h->pending) SS_CUDA(cudaEventSynchronize(h->ev_done));  // statistics of the previous call

@@ -120,6 +120,50 @@ __device__ __forceinline__ void finish_iteration_block(const Dev& d, unsigned lo
   }
 }
 
+// Root state and control block of a new single-source run (one thread).
+__device__ __forceinline__ void init_root_state(const Dev& d, int root) {
+  const int r = d.invperm[root];
+  d.lvl[r] = 0;
+  d.fb[0][r >> 5] |= 1u << (r & 31);
+  d.fr[r] = 1.0f;
+  d.par[r] = root + 1;
+  Ctl* c = d.ctl;
+  c->k = 1; c->done = 0; c->error = 0; c->variant = -1;
+  c->new_count = 0; c->new_deg = 0; c->slots = 0; c->active = 0;
+  c->reached = 1; c->reached_deg = (unsigned long long)d.rdeg[r];
+  c->total_slots = 0; c->dp_slots = 0; c->blocks_done = 0;
+  c->prev_variant = -1; c->prev_slots = 0; c->prev_new = 1; c->prev_deg = (unsigned long long)d.rdeg[r];
+  c->prev2_new = 0; c->prev_active = 0; c->new_maxdeg = 0; c->prev_maxdeg = (unsigned)d.rdeg[r];
+  c->units = 0;
+  for (int v = 0; v < 4; ++v) c->variant_count[v] = 0;
+  c->loop_guard = 0;
+  ss_iter_stats s;
+  s.frontier = 1; s.frontier_degree = d.rdeg[r]; s.slots = 0; s.active_chunks = 0;
+  s.variant = -1; s.kernel_ns = 0;
+  d.iters[0] = s;
+}
+
+// Distances and parents in original vertex ids (grid-stride over vertices).
+__device__ __forceinline__ void write_outputs(const Dev& d, int* dist, int* parent) {
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < d.n;
+       v += (long long)gridDim.x * blockDim.x) {
+    const int r = d.invperm[v];
+    const int L = d.lvl[r];
+    if (dist) dist[v] = (L == SS_INF) ? -1 : L;
+    if (parent) parent[v] = (L == SS_INF) ? -1 : d.par[r] - 1;
+  }
+}
+
+__global__ void k_init(Dev d);
+
+// Grid sizes that follow the graph size (ss_bfs.cu).
+int pull_grid(const slimsell_graph* h);
+int vertex_grid(const slimsell_graph* h, int threads);
+
+// Add a device-side iteration loop (conditional WHILE node) to graph g (ss_bfs.cu).
+ss_status add_loop_node(slimsell_graph* h, const Dev& d, int sr, int policy, cudaGraph_t g,
+                        const cudaGraphNode_t* deps, size_t ndeps, cudaGraphNode_t* out);
+
 // Launchers implemented in the other translation units.
 ss_status launch_push(const slimsell_graph* h, const Dev& d, int sr, const IterLaunch& il,
                       cudaStream_t st);

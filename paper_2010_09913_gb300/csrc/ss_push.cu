@@ -16,6 +16,8 @@
 //                   frontier word of level k (fb[k&1] held level k-2, which is
 //                   overwritten), and each touched row gets level k, parent and
 //                   value; the scratch is reset and the iteration tail runs.
+#include <algorithm>
+
 #include "ss_device.cuh"
 
 namespace ss {
@@ -152,10 +154,13 @@ __global__ void __launch_bounds__(PUSH_THREADS) k_push_post(Dev d, IterLaunch il
 template <int SR, int C>
 static ss_status launch_push_c(const slimsell_graph* h, const Dev& d, const IterLaunch& il,
                                cudaStream_t st) {
-  const int g = 8 * h->num_sms;
-  k_push_expand<<<g, PUSH_THREADS, 0, st>>>(d);
-  k_push_scatter<SR, C><<<g, PUSH_THREADS, 0, st>>>(d);
-  k_push_post<SR><<<8 * h->num_sms, PUSH_THREADS, 0, st>>>(d, il);
+  // grids follow the graph size: bitmap words for expand/post, possible units for scatter
+  const int gw = vertex_grid(h, 32 * PUSH_THREADS);
+  const long long units = (long long)h->n_pad + h->nnz / PUSH_UNIT;
+  const int gs = (int)std::max(1LL, std::min((long long)8 * h->num_sms, (units + 7) / 8));
+  k_push_expand<<<gw, PUSH_THREADS, 0, st>>>(d);
+  k_push_scatter<SR, C><<<gs, PUSH_THREADS, 0, st>>>(d);
+  k_push_post<SR><<<gw, PUSH_THREADS, 0, st>>>(d, il);
   SS_CUDA(cudaGetLastError());
   return SS_OK;
 }
