@@ -296,6 +296,71 @@ def batched_learned(ss, torch, g, h, roots, args, stream, dev, runs_edges):
     return out
 
 
+def batched_graphs(ss, torch, ngraphs, stream, dev):
+    """Many Kronecker graphs of uneven size (scales drawn from 10..18), one root
+    each: layout parameters autotuned once per scale, then every BFS one after
+    another vs all of them in one CUDA-graph launch."""
+    from paper_2010_09913_gb300 import autotune
+    rng = np.random.default_rng(17)
+    scales = rng.integers(10, 19, ngraphs)
+    graphs = [gg.kronecker(int(s), seed=1000 + i) for i, s in enumerate(scales)]
+    t0 = time.perf_counter()
+    tuned = {}
+    for s in sorted(set(int(x) for x in scales)):
+        g = graphs[int(np.flatnonzero(scales == s)[0])]
+        best, _ = autotune.tune(g.row_ptr, g.col, gg.roots(g, 2, seed=3), "tropical", "slimwork",
+                                repeats=2)
+        tuned[s] = best
+    tune_s = time.perf_counter() - t0
+    handles = []
+    for g, s in zip(graphs, scales):
+        p = tuned[int(s)]
+        rp = torch.from_numpy(g.row_ptr).to(dev)
+        cl = torch.from_numpy(g.col).to(dev)
+        sigma = g.n if p["sigma"] == "n" else int(p["sigma"])
+        handles.append(ss.slimsell_build(rp, cl, g.n, g.nnz, p["C"], sigma, p["split_w"], stream))
+    roots = [int(gg.roots(g, 1, seed=2)[0]) for g in graphs]
+    r_d = torch.tensor(roots, dtype=torch.int32, device=dev)
+    out = {"graphs": ngraphs, "scales": {int(s): int((scales == s).sum()) for s in sorted(set(scales))},
+           "tuned": {str(k): v for k, v in tuned.items()}, "autotune_seconds": tune_s,
+           "unit": "GTEPS"}
+    # every BFS one after another (device-side loops)
+    for h, r in zip(handles, roots):
+        ss.slimsell_bfs(h, r, SR_ID["tropical"], ss.V_SLIMWORK, None, None, stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for h, r in zip(handles, roots):
+        ss.slimsell_bfs(h, r, SR_ID["tropical"], ss.V_SLIMWORK, None, None, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1)
+    edges = 0
+    for policy in ("slimwork", "heuristic"):
+        b = ss.slimsell_batch_create(handles, SR_ID["tropical"], ss.POLICIES[policy])
+        ss.slimsell_batch_run(b, r_d, None, None, stream)
+        stats = ss.slimsell_batch_get_stats(b, ngraphs)
+        edges = sum(st.reached_degree // 2 for st in stats)
+        reps = 5
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            ss.slimsell_batch_run(b, r_d, None, None, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[f"batch_{policy}_ms"] = ms
+        out[f"batch_{policy}"] = edges / (ms / 1000.0) / 1e9
+        ss.slimsell_batch_destroy(b)
+    out["sequential_slimwork_ms"] = seq_ms
+    out["sequential_slimwork"] = edges / (seq_ms / 1000.0) / 1e9
+    out["edges"] = edges
+    for h in handles:
+        ss.slimsell_destroy(h)
+    return out
+
+
 def roofline_at_scale(ss, torch, scale, nroots, split_w, stream, dev):
     """Plain single-source SlimSell BFS (SlimWork + SlimChunk) at a larger scale:
     iteration-kernel GB/s from per-launch CUDA events, and whole-run GTEPS."""
@@ -350,6 +415,7 @@ def main():
     ap.add_argument("--no-ablations", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-scale24", action="store_true")
+    ap.add_argument("--batch-graphs", type=int, default=200)
     args = ap.parse_args()
     world, rank, local, pg = dist_setup()
     if args.impl == "reference":
@@ -476,6 +542,7 @@ def main():
     if not args.no_batched and rank == 0:
         line["batched_learned"] = batched_learned(ss, torch, g, h, roots, args, stream, dev,
                                                   edges_per_step)
+        line["batched_graphs"] = batched_graphs(ss, torch, args.batch_graphs, stream, dev)
     if not args.no_e2e:
         line["e2e"] = e2e_measure(ss, torch, g, roots, args, stream, dev, pg)
     if not args.no_ablations and rank == 0:
