@@ -59,11 +59,19 @@ typedef enum {
   SS_V_FULL = 0,          /* every chunk, every column (plain BFS-SpMV, Section III-A)        */
   SS_V_SLIMWORK = 1,      /* skip chunks whose rows are all visited (SlimWork, Section III-C) */
   SS_V_PUSH = 2,          /* compacted-frontier push (work-avoidance variant, Section V); falls
-                             back to PULL_FILTERED when the frontier exceeds the unit buffer  */
+                             back to PULL_FILTERED when the frontier exceeds the unit buffer;
+                             frontiers of at most 8192 vertices and 65536 edges run in the
+                             single-block push (SS_VARIANT_PUSH_LOCAL)                          */
   SS_V_PULL_FILTERED = 3, /* pull over unvisited rows only, stopping at the first hit         */
   SS_V_HEURISTIC = 4,     /* per-iteration choice by a frontier-size rule                      */
   SS_V_LEARNED = 5        /* per-iteration choice by the loaded selector MLP                   */
 } ss_policy;
+
+/* Executed-variant id (ss_iter_stats.variant, not a policy) of the single-block
+ * push: one 1024-thread block runs consecutive small levels in one launch with
+ * the frontier kept as a vertex list; push and the adaptive policies use it for
+ * frontiers of at most 8192 vertices and 65536 edges (high-diameter graphs). */
+#define SS_VARIANT_PUSH_LOCAL 4
 
 /* Layout summary of a built handle. */
 typedef struct {
@@ -84,7 +92,8 @@ typedef struct {
   int64_t frontier_degree; /* sum of their degrees                                    */
   int64_t slots;           /* col slots read by the iteration kernels                 */
   int64_t active_chunks;   /* chunks processed (not skipped)                          */
-  int32_t variant;         /* variant actually executed (0 FULL, 1 SLIMWORK, 2 PUSH, 3 FILTERED) */
+  int32_t variant;         /* variant actually executed (0 FULL, 1 SLIMWORK, 2 PUSH, 3 FILTERED,
+                              SS_VARIANT_PUSH_LOCAL)                                     */
   int32_t kernel_ns;       /* iteration kernel time in ns when profiling is on, else 0 */
 } ss_iter_stats;
 

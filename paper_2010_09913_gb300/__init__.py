@@ -18,6 +18,7 @@ from .build import LIB, build  # noqa: F401  (build() compiles the library)
 TROPICAL, REAL, BOOLEAN, SELMAX = 0, 1, 2, 3
 SEMIRINGS = {"tropical": TROPICAL, "real": REAL, "boolean": BOOLEAN, "selmax": SELMAX}
 V_FULL, V_SLIMWORK, V_PUSH, V_PULL_FILTERED, V_HEURISTIC, V_LEARNED = range(6)
+VARIANT_PUSH_LOCAL = 4  # executed-variant id of the single-block push (iteration stats only)
 POLICIES = {"full": V_FULL, "slimwork": V_SLIMWORK, "push": V_PUSH,
             "pull_filtered": V_PULL_FILTERED, "heuristic": V_HEURISTIC, "learned": V_LEARNED}
 STATUS = {0: "SS_OK", 1: "SS_ERR_INVALID", 2: "SS_ERR_OOM", 3: "SS_ERR_CUDA",

@@ -559,13 +559,16 @@ static ss_status launch_iteration(const slimsell_graph* h, const Dev& d, int sr,
   }
 }
 
-// Queue the kernels of one iteration of the given variant.
+// Queue the kernels of one iteration of the given variant.  The single-block
+// push runs as many small levels as it can in the device-side loop, and one
+// level per launch when the host drives the loop (per-level timing).
 static ss_status launch_variant(const slimsell_graph* h, const Dev& d, int sr, int variant,
                                 const IterLaunch& il, cudaStream_t st) {
   switch (variant) {
     case VAR_FULL: return launch_iteration(h, d, sr, MODE_FULL, il, st);
     case VAR_SLIMWORK: return launch_iteration(h, d, sr, MODE_SLIMWORK, il, st);
     case VAR_PUSH: return launch_push(h, d, sr, il, st);
+    case VAR_PUSH_LOCAL: return launch_push_local(h, d, sr, il, il.use_cond ? (1 << 30) : 1, st);
     default: return launch_iteration(h, d, sr, MODE_FILTERED, il, st);
   }
 }
@@ -595,16 +598,11 @@ static ss_status capture_into(slimsell_graph* h, const Dev& d, int sr, int varia
   return SS_OK;
 }
 
-// Device-side iteration loop: one conditional WHILE node whose body is either
-// the fixed variant's kernels, or (adaptive policies) the decide kernel
-// followed by a SWITCH node over the four variants.  The last block of each
-// iteration's final kernel sets the WHILE condition.  Built once per
-// (semiring, policy, staged-prefix size) and cached in the handle.
 // Add one device-side iteration loop to graph g after the given dependencies:
 // a conditional WHILE node whose body is the fixed variant's kernels, or (adaptive
-// policies) the decide kernel followed by a conditional SWITCH over the four
-// variants.  The last block of each iteration's final kernel sets the WHILE
-// condition.
+// policies) the decide kernel followed by a conditional SWITCH over the five
+// executed variants.  The last block of each iteration's final kernel (or the
+// single-block push, when it stops or hands back) sets the WHILE condition.
 ss_status add_loop_node(slimsell_graph* h, const Dev& d, int sr, int policy, cudaGraph_t g,
                         const cudaGraphNode_t* deps, size_t ndeps, cudaGraphNode_t* out) {
   cudaGraphConditionalHandle cw;
@@ -630,10 +628,10 @@ ss_status add_loop_node(slimsell_graph* h, const Dev& d, int sr, int policy, cud
   sp.type = cudaGraphNodeTypeConditional;
   sp.conditional.handle = csw;
   sp.conditional.type = cudaGraphCondTypeSwitch;
-  sp.conditional.size = 4;
+  sp.conditional.size = N_VARIANTS;
   e = cudaGraphAddNode(&snode, body, &dnode, nullptr, 1, &sp);
   if (e != cudaSuccess) return cuda_fail(e, "conditional SWITCH node");
-  for (int v = 0; v < 4 && s == SS_OK; ++v)
+  for (int v = 0; v < N_VARIANTS && s == SS_OK; ++v)
     s = capture_into(h, d, sr, v, IterLaunch{v, cw, 1}, sp.conditional.phGraph_out[v]);
   return s;
 }

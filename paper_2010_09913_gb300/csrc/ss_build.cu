@@ -542,6 +542,8 @@ static ss_status alloc_state(slimsell_graph* h) {
   if ((s = dmalloc(h, (void**)&h->pbest, sizeof(int) * np)) != SS_OK) return s;
   if ((s = dmalloc(h, (void**)&h->psum, sizeof(float) * np)) != SS_OK) return s;
   if ((s = dmalloc(h, (void**)&h->touched, sizeof(unsigned) * (size_t)h->fb_words)) != SS_OK) return s;
+  for (int b = 0; b < 2; ++b)
+    if ((s = dmalloc(h, (void**)&h->qlist[b], sizeof(int) * np)) != SS_OK) return s;
   SS_CUDA(cudaMemset(h->pbest, 0xff, sizeof(int) * np));
   SS_CUDA(cudaMemset(h->psum, 0, sizeof(float) * np));
   SS_CUDA(cudaMemset(h->touched, 0, sizeof(unsigned) * (size_t)h->fb_words));
@@ -568,7 +570,7 @@ void free_handle(slimsell_graph* h) {
   void* ptrs[] = {h->perm, h->invperm, h->rdeg, h->cl, h->cs, h->col, h->items, h->split_n,
                   h->lvl, h->act, h->fb[0], h->fb[1], h->fr, h->par, h->xacc, h->xpar,
                   h->arrive, h->ctl, h->iters, h->units, h->pbest,
-                  h->psum, h->touched, h->mlp, h->feats, h->mF[0], h->mF[1], h->mV,
+                  h->psum, h->touched, h->qlist[0], h->qlist[1], h->mlp, h->feats, h->mF[0], h->mF[1], h->mV,
                   h->mxacc, h->mroots};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -602,6 +604,7 @@ ss::Dev slimsell_graph::dev() const {
   d.fr = fr; d.par = par; d.xacc = xacc; d.xpar = xpar; d.arrive = arrive;
   d.units = units; d.units_cap = units_cap;
   d.pbest = pbest; d.psum = psum; d.touched = touched; d.mlp = mlp; d.feats = feats;
+  d.qlist[0] = qlist[0]; d.qlist[1] = qlist[1];
   d.nnz = nnz; d.total_slots = slots; d.reach_cap = (unsigned long long)n;
   d.ctl = ctl; d.iters = iters; d.iter_cap = iter_cap;
   return d;

@@ -51,7 +51,11 @@ struct Ctl {
   unsigned int new_maxdeg;        // largest degree discovered by the current iteration
   unsigned int prev_maxdeg;       // ... by the previous iteration
   unsigned long long units;       // push work units queued by the current iteration
-  unsigned long long variant_count[4];  // iterations run with each variant
+  unsigned long long variant_count[5];  // iterations run with each variant
+  int list_level;                 // level whose vertex list is in qlist[level & 1] (-1: none)
+  int list_prev_ok;               // qlist also holds the list of list_level - 1
+  unsigned long long qlen[2];     // vertex-list lengths, by level parity
+  unsigned long long qprep;       // length of a list just built from the bitmap
   unsigned long long loop_guard;  // decide-kernel executions in this run (device loop bound)
 };
 
@@ -81,6 +85,7 @@ struct Dev {
   int* pbest;           // [n_pad] push: largest frontier-neighbour original id (-1 = none)
   float* psum;          // [n_pad] push: real-semiring sum of frontier-neighbour values
   unsigned* touched;    // [fb_words] push: rows reached by the current push
+  int* qlist[2];        // [n_pad] vertex lists of a level (single-block push), by parity
   const float* mlp;     // selector weights (16-64-64-4 MLP), or NULL
   float* feats;         // [iter_cap][16] selector features of each iteration of the last run
   long long nnz, total_slots;
@@ -122,6 +127,7 @@ struct slimsell_graph {
   int* pbest = nullptr;
   float* psum = nullptr;
   unsigned* touched = nullptr;
+  int* qlist[2] = {nullptr, nullptr};
   float* mlp = nullptr;       // selector weights on the device (NULL until loaded)
   float* feats = nullptr;
   // multi-source scratch ([n_pad][W] words), grown on demand

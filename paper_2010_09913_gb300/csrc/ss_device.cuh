@@ -5,9 +5,14 @@
 
 namespace ss {
 
-// Variant ids executed by one iteration (the values of ss_policy 0..3).
+// Variant ids executed by one iteration (0..3 are the ss_policy values; 4 is
+// the single-block push that runs several small levels in one launch).
 enum { VAR_FULL = SS_V_FULL, VAR_SLIMWORK = SS_V_SLIMWORK, VAR_PUSH = SS_V_PUSH,
-       VAR_FILTERED = SS_V_PULL_FILTERED };
+       VAR_FILTERED = SS_V_PULL_FILTERED, VAR_PUSH_LOCAL = 4, N_VARIANTS = 5 };
+
+// Frontiers at most this large (vertices, edges) go to the single-block push.
+constexpr int LOCAL_MAX_FRONTIER = 8192;
+constexpr int LOCAL_MAX_EDGES = 1 << 16;
 
 struct IterLaunch {
   int variant;
@@ -15,20 +20,13 @@ struct IterLaunch {
   int use_cond;
 };
 
-// End of an iteration, run by the last block of its final kernel: record the
-// statistics, test convergence, advance k and (device-side loop) set the loop
-// condition.  The loop also stops, flagging an error, if k passes n + 1 or more
-// than n vertices were counted, which a correct BFS never does, so the device
-// loop always terminates.
-__device__ __forceinline__ void iteration_tail(const Dev& d, int variant,
-                                               cudaGraphConditionalHandle cond, int use_cond) {
-  Ctl* c = d.ctl;
-  const int k = c->k;
-  const unsigned long long nc = atomicAdd(&c->new_count, 0ull);
-  const unsigned long long nd = atomicAdd(&c->new_deg, 0ull);
-  const unsigned long long sl = atomicAdd(&c->slots, 0ull);
-  const unsigned long long ac = atomicAdd(&c->active, 0ull);
-  const unsigned md = atomicMax(&c->new_maxdeg, 0u);
+// Record the finished level k (nc vertices discovered, nd their degree sum, sl
+// slots read, ac chunks processed, md largest new degree) and advance k.
+// Returns true when the run must stop: an iteration that discovered nothing,
+// or (an error) k past n + 1 or more units reached than a correct run can count.
+__device__ __forceinline__ bool advance_level(const Dev& d, Ctl* c, int k, unsigned long long nc,
+                                              unsigned long long nd, unsigned long long sl,
+                                              unsigned long long ac, unsigned md, int variant) {
   if (k < d.iter_cap) {
     ss_iter_stats s;
     s.frontier = (long long)nc;
@@ -50,20 +48,38 @@ __device__ __forceinline__ void iteration_tail(const Dev& d, int variant,
   c->prev_maxdeg = md;
   c->prev_variant = variant;
   c->variant = variant;
-  if (variant >= 0 && variant < 4) c->variant_count[variant] += 1;
+  if (variant >= 0 && variant < N_VARIANTS) c->variant_count[variant] += 1;
   c->units = 0;
+  c->qprep = 0;
   bool stop = (nc == 0);
   if (k >= d.n + 1 || c->reached > d.reach_cap) {
     c->error |= 1;
     stop = true;
   }
   if (stop) c->done = 1;
+  c->k = k + 1;
+  return stop;
+}
+
+// End of an iteration, run by the last block of its final kernel: record the
+// level, reset the per-iteration counters and (device-side loop) set the loop
+// condition.  The vertex list of the single-block push is no longer current.
+__device__ __forceinline__ void iteration_tail(const Dev& d, int variant,
+                                               cudaGraphConditionalHandle cond, int use_cond) {
+  Ctl* c = d.ctl;
+  const int k = c->k;
+  const unsigned long long nc = atomicAdd(&c->new_count, 0ull);
+  const unsigned long long nd = atomicAdd(&c->new_deg, 0ull);
+  const unsigned long long sl = atomicAdd(&c->slots, 0ull);
+  const unsigned long long ac = atomicAdd(&c->active, 0ull);
+  const unsigned md = atomicMax(&c->new_maxdeg, 0u);
+  const bool stop = advance_level(d, c, k, nc, nd, sl, ac, md, variant);
+  c->list_level = -1;
   c->new_count = 0;
   c->new_deg = 0;
   c->slots = 0;
   c->active = 0;
   c->new_maxdeg = 0;
-  c->k = k + 1;
   c->blocks_done = 0;
   __threadfence();
   if (use_cond) cudaGraphSetConditional(cond, stop ? 0u : 1u);
@@ -135,8 +151,9 @@ __device__ __forceinline__ void init_root_state(const Dev& d, int root) {
   c->prev_variant = -1; c->prev_slots = 0; c->prev_new = 1; c->prev_deg = (unsigned long long)d.rdeg[r];
   c->prev2_new = 0; c->prev_active = 0; c->new_maxdeg = 0; c->prev_maxdeg = (unsigned)d.rdeg[r];
   c->units = 0;
-  for (int v = 0; v < 4; ++v) c->variant_count[v] = 0;
+  for (int v = 0; v < N_VARIANTS; ++v) c->variant_count[v] = 0;
   c->loop_guard = 0;
+  c->list_level = -1; c->list_prev_ok = 0; c->qlen[0] = c->qlen[1] = 0; c->qprep = 0;
   ss_iter_stats s;
   s.frontier = 1; s.frontier_degree = d.rdeg[r]; s.slots = 0; s.active_chunks = 0;
   s.variant = -1; s.kernel_ns = 0;
@@ -167,8 +184,8 @@ ss_status add_loop_node(slimsell_graph* h, const Dev& d, int sr, int policy, cud
 // Launchers implemented in the other translation units.
 ss_status launch_push(const slimsell_graph* h, const Dev& d, int sr, const IterLaunch& il,
                       cudaStream_t st);
-ss_status launch_pull_variant(const slimsell_graph* h, const Dev& d, int sr, int variant,
-                              const IterLaunch& il, cudaStream_t st);
+ss_status launch_push_local(const slimsell_graph* h, const Dev& d, int sr, const IterLaunch& il,
+                            int max_levels, cudaStream_t st);
 ss_status launch_decide(const slimsell_graph* h, const Dev& d, int policy,
                         cudaGraphConditionalHandle sw, int use_sw, cudaStream_t st);
 ss_status add_decide_node(const slimsell_graph* h, const Dev& d, int policy,

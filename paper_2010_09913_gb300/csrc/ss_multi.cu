@@ -167,7 +167,8 @@ __global__ void k_multi_roots(MultiDev m, int W) {
     c->prev_variant = -1; c->prev_slots = 0; c->prev_new = (unsigned long long)m.k; c->prev_deg = rd;
     c->prev2_new = 0; c->prev_active = 0; c->new_maxdeg = 0; c->prev_maxdeg = 0; c->units = 0;
     c->loop_guard = 0;
-    for (int v = 0; v < 4; ++v) c->variant_count[v] = 0;
+    for (int v = 0; v < N_VARIANTS; ++v) c->variant_count[v] = 0;
+    c->list_level = -1; c->list_prev_ok = 0; c->qlen[0] = c->qlen[1] = 0; c->qprep = 0;
     ss_iter_stats st;
     st.frontier = m.k; st.frontier_degree = (long long)rd; st.slots = 0; st.active_chunks = 0;
     st.variant = -1; st.kernel_ns = 0;

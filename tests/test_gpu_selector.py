@@ -59,9 +59,11 @@ def test_push_then_pull_schedules_mix():
     r = int(gg.roots(g, 1, seed=2)[0])
     G.bfs(r, "tropical", "heuristic")
     seq = variants_of(G, 64)
-    assert seq[0] == ss.V_PUSH and ss.V_PULL_FILTERED in seq, seq
+    assert seq[0] in (ss.V_PUSH, ss.VARIANT_PUSH_LOCAL) and ss.V_PULL_FILTERED in seq, seq
     G.bfs(r, "tropical", "push")
-    assert all(v == ss.V_PUSH for v in variants_of(G, 64))
+    seq = variants_of(G, 64)
+    assert all(v in (ss.V_PUSH, ss.VARIANT_PUSH_LOCAL) for v in seq), seq
+    assert ss.V_PUSH in seq and ss.VARIANT_PUSH_LOCAL in seq, seq
     ss.slimsell_selector_load(G.h, gg.mlp_weights(11, scale=3.0))
     G.bfs(r, "boolean", "learned")
     assert len(set(variants_of(G, 64))) >= 1
