@@ -11,6 +11,7 @@
 #include <cstring>
 #include <vector>
 
+#include "ss_device.cuh"
 #include "ss_sort.cuh"
 
 namespace ss {
@@ -542,8 +543,20 @@ static ss_status alloc_state(slimsell_graph* h) {
   if ((s = dmalloc(h, (void**)&h->pbest, sizeof(int) * np)) != SS_OK) return s;
   if ((s = dmalloc(h, (void**)&h->psum, sizeof(float) * np)) != SS_OK) return s;
   if ((s = dmalloc(h, (void**)&h->touched, sizeof(unsigned) * (size_t)h->fb_words)) != SS_OK) return s;
-  for (int b = 0; b < 2; ++b)
+  for (int b = 0; b < 2; ++b) {
     if ((s = dmalloc(h, (void**)&h->qlist[b], sizeof(int) * np)) != SS_OK) return s;
+    if ((s = dmalloc(h, (void**)&h->qdeg[b], sizeof(int) * SS_LOCAL_LIST_CAP)) != SS_OK) return s;
+    if ((s = dmalloc(h, (void**)&h->qbase[b], sizeof(long long) * SS_LOCAL_LIST_CAP)) != SS_OK) return s;
+    if ((s = dmalloc(h, (void**)&h->qorig[b], sizeof(int) * SS_LOCAL_LIST_CAP)) != SS_OK) return s;
+  }
+  if ((s = dmalloc(h, (void**)&h->qovf, sizeof(int) * SS_LOCAL_LIST_CAP)) != SS_OK) return s;
+  if ((s = dmalloc(h, (void**)&h->qovf_n, 2 * sizeof(unsigned long long))) != SS_OK) return s;
+  SS_CUDA(cudaMemset(h->qovf_n, 0, 2 * sizeof(unsigned long long)));
+  h->local_cluster = push_local_cluster_size();
+  if (h->local_cluster <= 0) {
+    set_error("slimsell_build: no thread-block cluster of the push kernel fits on this device");
+    return SS_ERR_CUDA;
+  }
   SS_CUDA(cudaMemset(h->pbest, 0xff, sizeof(int) * np));
   SS_CUDA(cudaMemset(h->psum, 0, sizeof(float) * np));
   SS_CUDA(cudaMemset(h->touched, 0, sizeof(unsigned) * (size_t)h->fb_words));
@@ -570,8 +583,9 @@ void free_handle(slimsell_graph* h) {
   void* ptrs[] = {h->perm, h->invperm, h->rdeg, h->cl, h->cs, h->col, h->items, h->split_n,
                   h->lvl, h->act, h->fb[0], h->fb[1], h->fr, h->par, h->xacc, h->xpar,
                   h->arrive, h->ctl, h->iters, h->units, h->pbest,
-                  h->psum, h->touched, h->qlist[0], h->qlist[1], h->mlp, h->feats, h->mF[0], h->mF[1], h->mV,
-                  h->mxacc, h->mroots};
+                  h->psum, h->touched, h->qlist[0], h->qlist[1], h->qdeg[0], h->qdeg[1], h->qbase[0],
+                  h->qbase[1], h->qorig[0], h->qorig[1], h->qovf, h->qovf_n, h->mlp, h->feats, h->mF[0],
+                  h->mF[1], h->mV, h->mxacc, h->mroots};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->h_ctl) cudaFreeHost(h->h_ctl);
@@ -604,7 +618,13 @@ ss::Dev slimsell_graph::dev() const {
   d.fr = fr; d.par = par; d.xacc = xacc; d.xpar = xpar; d.arrive = arrive;
   d.units = units; d.units_cap = units_cap;
   d.pbest = pbest; d.psum = psum; d.touched = touched; d.mlp = mlp; d.feats = feats;
-  d.qlist[0] = qlist[0]; d.qlist[1] = qlist[1];
+  for (int b = 0; b < 2; ++b) {
+    d.qlist[b] = qlist[b]; d.qdeg[b] = qdeg[b]; d.qbase[b] = qbase[b]; d.qorig[b] = qorig[b];
+  }
+  d.qovf = qovf; d.qovf_n = qovf_n;
+  d.local_cluster = local_cluster;
+  d.local_max_nf = (long long)local_cluster * SS_LOCAL_SLICE;
+  d.local_max_e = (long long)local_cluster * SS_LOCAL_EDGES_PER_CTA;
   d.nnz = nnz; d.total_slots = slots; d.reach_cap = (unsigned long long)n;
   d.ctl = ctl; d.iters = iters; d.iter_cap = iter_cap;
   return d;

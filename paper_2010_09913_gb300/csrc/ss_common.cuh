@@ -15,6 +15,11 @@
 #define SS_FULL_MASK 0xffffffffu
 #define SS_SMEM_MAX_BYTES 212992   // frontier-bitmap prefix staged per block (1,703,936 vertices)
 #define SS_SMEM_LIMIT_BYTES 214016 // dynamic shared memory requested at most (prefix + guard)
+// cluster push: frontier entries and frontier edges per CTA, largest cluster, list capacity
+#define SS_LOCAL_SLICE 4096
+#define SS_LOCAL_EDGES_PER_CTA 8192
+#define SS_LOCAL_CLUSTER_MAX 16
+#define SS_LOCAL_LIST_CAP (SS_LOCAL_CLUSTER_MAX * SS_LOCAL_EDGES_PER_CTA)
 
 namespace ss {
 
@@ -85,7 +90,14 @@ struct Dev {
   int* pbest;           // [n_pad] push: largest frontier-neighbour original id (-1 = none)
   float* psum;          // [n_pad] push: real-semiring sum of frontier-neighbour values
   unsigned* touched;    // [fb_words] push: rows reached by the current push
-  int* qlist[2];        // [n_pad] vertex lists of a level (single-block push), by parity
+  int* qlist[2];        // [n_pad] vertex lists of a level (cluster push), by parity
+  int* qdeg[2];         // [SS_LOCAL_LIST_CAP] cluster push: degree of each listed vertex
+  long long* qbase[2];  // [SS_LOCAL_LIST_CAP] ... start of its column-major row (cs + row % C)
+  int* qorig[2];        // [SS_LOCAL_LIST_CAP] ... its original id
+  int* qovf;            // [SS_LOCAL_LIST_CAP] cluster push: new vertices past a CTA's list
+  unsigned long long* qovf_n;  // [2] their counts, by level parity
+  int local_cluster;    // CTAs in the cluster push's cluster
+  long long local_max_nf, local_max_e;  // largest frontier (vertices, edges) it takes
   const float* mlp;     // selector weights (16-64-64-4 MLP), or NULL
   float* feats;         // [iter_cap][16] selector features of each iteration of the last run
   long long nnz, total_slots;
@@ -128,6 +140,12 @@ struct slimsell_graph {
   float* psum = nullptr;
   unsigned* touched = nullptr;
   int* qlist[2] = {nullptr, nullptr};
+  int* qdeg[2] = {nullptr, nullptr};
+  long long* qbase[2] = {nullptr, nullptr};
+  int* qorig[2] = {nullptr, nullptr};
+  int* qovf = nullptr;
+  unsigned long long* qovf_n = nullptr;
+  int local_cluster = 0;
   float* mlp = nullptr;       // selector weights on the device (NULL until loaded)
   float* feats = nullptr;
   // multi-source scratch ([n_pad][W] words), grown on demand

@@ -6,13 +6,15 @@
 namespace ss {
 
 // Variant ids executed by one iteration (0..3 are the ss_policy values; 4 is
-// the single-block push that runs several small levels in one launch).
+// the cluster push that runs several small levels in one launch).
 enum { VAR_FULL = SS_V_FULL, VAR_SLIMWORK = SS_V_SLIMWORK, VAR_PUSH = SS_V_PUSH,
        VAR_FILTERED = SS_V_PULL_FILTERED, VAR_PUSH_LOCAL = 4, N_VARIANTS = 5 };
 
-// Frontiers at most this large (vertices, edges) go to the single-block push.
-constexpr int LOCAL_MAX_FRONTIER = 8192;
-constexpr int LOCAL_MAX_EDGES = 1 << 16;
+// Frontiers the cluster push takes: at most d.local_max_nf vertices and
+// d.local_max_e edges (SS_LOCAL_SLICE and SS_LOCAL_EDGES_PER_CTA per CTA).
+__device__ __forceinline__ bool local_fits(const Dev& d, unsigned long long nf, unsigned long long mf) {
+  return nf <= (unsigned long long)d.local_max_nf && mf <= (unsigned long long)d.local_max_e;
+}
 
 struct IterLaunch {
   int variant;
@@ -24,10 +26,12 @@ struct IterLaunch {
 // slots read, ac chunks processed, md largest new degree) and advance k.
 // Returns true when the run must stop: an iteration that discovered nothing,
 // or (an error) k past n + 1 or more units reached than a correct run can count.
+// record = false keeps d.iters untouched (copies of the control block).
 __device__ __forceinline__ bool advance_level(const Dev& d, Ctl* c, int k, unsigned long long nc,
                                               unsigned long long nd, unsigned long long sl,
-                                              unsigned long long ac, unsigned md, int variant) {
-  if (k < d.iter_cap) {
+                                              unsigned long long ac, unsigned md, int variant,
+                                              bool record = true) {
+  if (record && k < d.iter_cap) {
     ss_iter_stats s;
     s.frontier = (long long)nc;
     s.frontier_degree = (long long)nd;
@@ -186,6 +190,7 @@ ss_status launch_push(const slimsell_graph* h, const Dev& d, int sr, const IterL
                       cudaStream_t st);
 ss_status launch_push_local(const slimsell_graph* h, const Dev& d, int sr, const IterLaunch& il,
                             int max_levels, cudaStream_t st);
+int push_local_cluster_size();  // CTAs per cluster of the cluster push on the current device (0: none)
 ss_status launch_decide(const slimsell_graph* h, const Dev& d, int policy,
                         cudaGraphConditionalHandle sw, int use_sw, cudaStream_t st);
 ss_status add_decide_node(const slimsell_graph* h, const Dev& d, int policy,

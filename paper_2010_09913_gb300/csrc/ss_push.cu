@@ -19,9 +19,13 @@
 #include <algorithm>
 #include <climits>
 
+#include <cooperative_groups.h>
+
 #include "ss_device.cuh"
 
 namespace ss {
+
+namespace cg = cooperative_groups;
 
 constexpr int PUSH_UNIT = 256;
 constexpr int PUSH_THREADS = 256;
@@ -153,50 +157,67 @@ __global__ void __launch_bounds__(PUSH_THREADS) k_push_post(Dev d, IterLaunch il
 }
 
 // ---------------------------------------------------------------------------
-// Single-block push for small frontiers: one 1024-thread block runs level after
-// level inside one launch (no kernel boundary, no bitmap walk per level).  The
-// frontier is a vertex list held in shared memory together with what the
-// scatter needs of each vertex (start of its column-major row, original id, the
-// prefix sum of degrees), so that a level costs few dependent global round
-// trips: the column loads, the level checks, one atomicMax per candidate edge
-// (whose old value -1 marks the first discoverer, which appends the vertex),
-// then one batch of loads in the post step.  Each thread takes a contiguous run
-// of the level's edges (one binary search, then a forward walk).  The control
-// block is worked on in shared memory and written back when the kernel ends.
-// The block hands back to the iteration loop when the frontier outgrows
-// LOCAL_MAX_FRONTIER vertices or LOCAL_MAX_EDGES edges, or after max_levels
-// levels, leaving the frontier bitmaps and lists as the grid-wide variants
-// and the next launch expect them:
+// Cluster push for small frontiers: one thread-block cluster (16 CTAs of 1024
+// threads where the device can place it, else 8) runs level after level inside
+// one launch, with no kernel boundary and no bitmap walk per level.  The
+// frontier is a vertex list in global memory with, per vertex, what the scatter
+// needs (degree, start of its column-major row, original id); each CTA takes an
+// equal slice of it into shared memory, scatters over the slice's edges (each
+// thread a contiguous run: one binary search, then a forward walk), and keeps
+// the vertices it discovers.  A vertex belongs to the CTA whose atomicMax on
+// its parent slot returned the initial -1.  Two hardware cluster barriers per
+// level order the scatter before the post step (which reads the final parents)
+// and the post step before the next level; per-CTA counts and statistics are
+// read across the cluster from distributed shared memory.  Spreading the
+// random gathers and atomics over many SMs is what makes a level cheap: one
+// SM's L1 serves about one uncoalesced line per clock.  Every CTA keeps a copy
+// of the control block in shared memory, updated identically from the cluster
+// totals, so all CTAs take the same exits; CTA 0 writes it back at the end.
+// The cluster hands back to the iteration loop when the frontier outgrows
+// d.local_max_nf vertices or d.local_max_e edges, or after max_levels levels,
+// leaving the bitmaps and lists as the grid-wide variants and the next launch
+// expect them:
 //   fb[(k-1)&1] = level k-1, fb[k&1] = level k-2 (or zero),
-//   qlist[(k-1)&1] = level k-1, qlist[k&1] = level k-2 (lengths in qlen).
+//   qlist/qdeg/qbase/qorig[(k-1)&1] = level k-1, qlist[k&1] = level k-2 (lengths in qlen).
 // ---------------------------------------------------------------------------
 constexpr int LOCAL_THREADS = 1024;
-constexpr int LOCAL_BATCH = 16;                                  // edges per thread in flight
-constexpr int LOCAL_PER_THREAD = LOCAL_MAX_FRONTIER / LOCAL_THREADS;  // frontier entries
+constexpr int LOCAL_BATCH = 16;     // candidate edges per thread in flight
+constexpr int LOCAL_NEWCAP = 8192;  // new vertices per CTA kept in shared memory
+constexpr int LOCAL_PER_THREAD = SS_LOCAL_SLICE / LOCAL_THREADS;
 constexpr int CTL_WORDS = (int)(sizeof(Ctl) / sizeof(unsigned));
 static_assert(sizeof(Ctl) % sizeof(unsigned) == 0, "control block copied as words");
-static_assert(LOCAL_MAX_FRONTIER % LOCAL_THREADS == 0, "whole frontier entries per thread");
+static_assert(SS_LOCAL_SLICE % LOCAL_THREADS == 0, "whole frontier entries per thread");
+
+struct LocalPub {             // what each CTA tells every CTA of the cluster about a level
+  int nsm;                    // new vertices it holds in shared memory
+  int novf;                   // new vertices it put in the overflow list
+  unsigned md;                // largest degree of its new vertices
+  unsigned long long nd;      // their degree sum
+};
 
 struct LocalSmem {
-  Ctl ctl;                               // working copy of the control block
-  long long base[LOCAL_MAX_FRONTIER];    // cs[u / C] + u % C
-  int ids[2][LOCAL_MAX_FRONTIER];        // frontier and next lists, by level parity
-  int pref[LOCAL_MAX_FRONTIER];          // degrees, then their exclusive prefix
-  int orig[LOCAL_MAX_FRONTIER];          // original id (the parent candidate)
+  Ctl ctl;                             // this CTA's copy of the control block
+  long long base[SS_LOCAL_SLICE];      // frontier slice: cs[u / C] + u % C
+  int pref[SS_LOCAL_SLICE];            // degrees, then their exclusive prefix
+  int orig[SS_LOCAL_SLICE];            // original ids (parent candidates)
+  int sid[2][SS_LOCAL_SLICE];          // vertex ids of the slice, by level parity
+  int nid[LOCAL_NEWCAP];               // vertices this CTA discovered
   long long wsum[LOCAL_THREADS / 32];
   unsigned long long red[LOCAL_THREADS / 32];
   unsigned redmax[LOCAL_THREADS / 32];
-  int nnew, stop;
+  LocalPub all[2][SS_LOCAL_CLUSTER_MAX];  // written by every CTA of the cluster, by level parity
+  long long off;                       // first list position of this CTA's new vertices
+  int nnew, novf, stop;
 };
-static_assert(sizeof(LocalSmem) <= 227 * 1024, "single-block push shared memory");
+static_assert(sizeof(LocalSmem) <= 227 * 1024, "cluster push shared memory");
 
 // Entry from a bitmap state: list the level-(k-1) rows into qlist[(k-1)&1] and
-// clear fb[k&1] (it held level k-2, which the single-block push does not list).
+// clear fb[k&1] (it held level k-2, which the cluster push does not list).
 __global__ void __launch_bounds__(PUSH_THREADS) k_push_local_prep(Dev d) {
   Ctl* c = d.ctl;
   if (c->done) return;
   const int k = c->k;
-  if (c->list_level == k - 1) return;  // the previous single-block level left its list
+  if (c->list_level == k - 1) return;  // the previous cluster-push level left its list
   const int lane = threadIdx.x & 31;
   const long long stride = (long long)gridDim.x * blockDim.x;
   const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -222,94 +243,130 @@ __global__ void __launch_bounds__(PUSH_THREADS) k_push_local_prep(Dev d) {
       unsigned long long base = 0;
       if (lane == 0) base = atomicAdd(&c->qprep, (unsigned long long)__popc(m));
       base = __shfl_sync(SS_FULL_MASK, base, 0);
-      if (u >= 0) list[base + __popc(m & ((1u << lane) - 1u))] = u;
+      // the decide kernel sends only frontiers that fit the list
+      const unsigned long long at = base + __popc(m & ((1u << lane) - 1u));
+      if (u >= 0 && at < (unsigned long long)d.n_pad) list[at] = u;
     }
   }
 }
 
-// End the kernel: write the working control block back and set the loop
-// condition (all threads call).
-__device__ __forceinline__ void local_exit(LocalSmem& S, Ctl* c, const IterLaunch& il, unsigned cond) {
-  __syncthreads();
+// End the kernel: no CTA leaves while another may still read its shared memory;
+// CTA 0 writes its control block back and sets the loop condition.
+__device__ __forceinline__ void local_exit(LocalSmem& S, Ctl* c, const IterLaunch& il, unsigned cond,
+                                           cg::cluster_group& cl) {
+  cl.sync();
+  if (cl.block_rank() != 0) return;
   const unsigned* src = reinterpret_cast<const unsigned*>(&S.ctl);
   unsigned* dst = reinterpret_cast<unsigned*>(c);
   for (int i = threadIdx.x; i < CTL_WORDS; i += LOCAL_THREADS) dst[i] = src[i];
   if (threadIdx.x == 0 && il.use_cond) cudaGraphSetConditional(il.cond, cond);
 }
 
-// Row data of vertex u into frontier slot i.
-template <int C>
-__device__ __forceinline__ void local_stage(LocalSmem& S, const Dev& d, int i, int u, int deg) {
-  S.pref[i] = deg;
-  S.base[i] = __ldg(d.cs + u / C) + (u % C);
-  S.orig[i] = __ldg(d.perm + u);
-}
-
 extern __shared__ __align__(16) unsigned char ss_local_smem[];
+
+// CTA r's first entry of a list of `total` entries split into G equal shares.
+__device__ __forceinline__ long long share(long long total, int r, int G) { return total * r / G; }
+
+// The CTA whose share holds list entry `at` (0 <= at < total).
+__device__ __forceinline__ int share_owner(long long at, long long total, int G) {
+  int r = (int)((at * G) / total);
+  while (r + 1 < G && share(total, r + 1, G) <= at) ++r;
+  while (r > 0 && share(total, r, G) > at) --r;
+  return r;
+}
 
 template <int SR, int C>
 __global__ void __launch_bounds__(LOCAL_THREADS, 1) k_push_local(Dev d, IterLaunch il, int max_levels) {
   constexpr int BATCH = (SR == SS_REAL) ? LOCAL_BATCH / 2 : LOCAL_BATCH;  // registers
   LocalSmem& S = *reinterpret_cast<LocalSmem*>(ss_local_smem);
-  Ctl* c = d.ctl;
-  if (c->done) return;
+  cg::cluster_group cl = cg::this_cluster();
+  const int G = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  Ctl* c = d.ctl;
   {
     const unsigned* src = reinterpret_cast<const unsigned*>(c);
     unsigned* dst = reinterpret_cast<unsigned*>(&S.ctl);
     for (int i = tid; i < CTL_WORDS; i += LOCAL_THREADS) dst[i] = src[i];
+    if (rank == 0 && tid < 2) d.qovf_n[tid] = 0ull;
   }
-  __syncthreads();
+  cl.sync();  // every CTA holds its copy before CTA 0 can write the block back
+  if (S.ctl.done) return;  // the same in every CTA; no shared memory was shared yet
   int k = S.ctl.k;
-  // the frontier list (level k-1): left by the previous launch, or just listed by
-  // k_push_local_prep (which also cleared fb[k&1])
   const bool have_list = S.ctl.list_level == k - 1;
-  int nf = (int)min(have_list ? S.ctl.qlen[(k - 1) & 1] : S.ctl.qprep, (unsigned long long)INT_MAX);
-  if (nf > LOCAL_MAX_FRONTIER) {  // the decide kernel never sends a frontier this large
+  long long nf = (long long)(have_list ? S.ctl.qlen[(k - 1) & 1] : S.ctl.qprep);
+  long long E = (long long)S.ctl.prev_deg;  // edges of the level-(k-1) frontier
+  if (!local_fits(d, (unsigned long long)nf, (unsigned long long)E)) {
+    // the decide kernel never sends such a frontier
     if (tid == 0) {
       S.ctl.error |= 8;
       S.ctl.done = 1;
     }
-    local_exit(S, c, il, 0u);
+    local_exit(S, c, il, 0u, cl);
     return;
   }
-  int cur = (k - 1) & 1;  // S.ids[cur] holds the frontier
-  {
-    const int* gl = d.qlist[(k - 1) & 1];
-    for (int i = tid; i < nf; i += LOCAL_THREADS) {
-      const int u = gl[i];
-      S.ids[cur][i] = u;
-      local_stage<C>(S, d, i, u, __ldg(d.rdeg + u));
-    }
-    // level k-2 words of fb[k&1], through the list the previous launch left
-    const int n2 = (have_list && S.ctl.list_prev_ok) ? (int)S.ctl.qlen[k & 1] : 0;
-    const int* g2 = d.qlist[k & 1];
-    unsigned* fbk = d.fb[k & 1];
-    for (int i = tid; i < n2; i += LOCAL_THREADS) fbk[g2[i] >> 5] = 0u;
-  }
   if (tid == 0 && !have_list) S.ctl.qlen[(k - 1) & 1] = (unsigned long long)nf;
-  __syncthreads();
-  int clear_n = 0;  // level k-2 entries of S.ids[cur ^ 1] to clear (after the first level)
+  // the first slice comes from the global list (its per-vertex data listed too, or
+  // gathered), and the level k-2 words to clear from the list the previous launch
+  // left; later slices arrive in shared memory from the CTAs that found them
+  {
+    const int p1 = (k - 1) & 1;
+    const long long lo = share(nf, rank, G);
+    const int ns = (int)(share(nf, rank + 1, G) - lo);
+    for (int i = tid; i < ns; i += LOCAL_THREADS) {
+      const int u = __ldcg(d.qlist[p1] + lo + i);
+      S.sid[p1][i] = u;
+      if (have_list) {
+        S.pref[i] = __ldcg(d.qdeg[p1] + lo + i);
+        S.base[i] = __ldcg(d.qbase[p1] + lo + i);
+        S.orig[i] = __ldcg(d.qorig[p1] + lo + i);
+      } else {
+        S.pref[i] = __ldg(d.rdeg + u);
+        S.base[i] = __ldg(d.cs + u / C) + (u % C);
+        S.orig[i] = __ldg(d.perm + u);
+      }
+    }
+    const long long n2 = (have_list && S.ctl.list_prev_ok) ? (long long)S.ctl.qlen[k & 1] : 0;
+    const long long lo2 = share(n2, rank, G), hi2 = share(n2, rank + 1, G);
+    unsigned* fbk = d.fb[k & 1];
+    for (long long i = lo2 + tid; i < hi2; i += LOCAL_THREADS) fbk[__ldcg(d.qlist[k & 1] + i) >> 5] = 0u;
+  }
+  int ns_prev = 0;  // entries of S.sid[k&1]: this CTA's slice of level k-2 (after the first level)
   for (int lev = 0;; ++lev) {
-    const bool give_back = lev >= max_levels || nf > LOCAL_MAX_FRONTIER;
-    long long E = 0;
-    if (!give_back) {  // exclusive prefix of the frontier degrees, in place
-      int dg[LOCAL_PER_THREAD];
-      long long sum = 0;
+    if (lev > 0 && (lev >= max_levels || !local_fits(d, (unsigned long long)nf, (unsigned long long)E))) {
+      if (tid == 0) {  // hand the level-(k-1) list back
+        S.ctl.list_level = k - 1;
+        S.ctl.list_prev_ok = 1;
+      }
+      local_exit(S, c, il, 1u, cl);
+      return;
+    }
+    const int p1 = (k - 1) & 1, p0 = k & 1;
+    unsigned* fbk = d.fb[p0];
+    const int ns = (int)(share(nf, rank + 1, G) - share(nf, rank, G));
+    for (int i = tid; i < ns_prev; i += LOCAL_THREADS) fbk[S.sid[p0][i] >> 5] = 0u;  // level k-2
+    if (tid == 0) {
+      S.nnew = 0;
+      S.novf = 0;
+    }
+    __syncthreads();
+    // ---- exclusive prefix of the slice's degrees, in place ----
+    int Es;
+    {
+      int dg[LOCAL_PER_THREAD], sum = 0;
 #pragma unroll
       for (int q = 0; q < LOCAL_PER_THREAD; ++q) {
         const int i = tid * LOCAL_PER_THREAD + q;
-        dg[q] = (i < nf) ? S.pref[i] : 0;
-        sum += dg[q];
+        dg[q] = (i < ns) ? S.pref[i] : 0;
+        sum += dg[q];  // the slice's edges are at most E <= d.local_max_e
       }
-      long long incl = sum;
+      int incl = sum;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        const long long t = __shfl_up_sync(SS_FULL_MASK, incl, o);
+        const int t = __shfl_up_sync(SS_FULL_MASK, incl, o);
         if (lane >= o) incl += t;
       }
       if (lane == 31) S.wsum[wid] = incl;
-      if (tid == 0) S.nnew = 0;
       __syncthreads();
       if (wid == 0) {
         long long w = S.wsum[lane];
@@ -321,54 +378,31 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) k_push_local(Dev d, IterLaun
         S.wsum[lane] = w;
       }
       __syncthreads();
-      E = S.wsum[LOCAL_THREADS / 32 - 1];
-      if (E <= LOCAL_MAX_EDGES) {  // then every prefix fits in int
-        long long run = (wid > 0 ? S.wsum[wid - 1] : 0LL) + incl - sum;
+      Es = (int)S.wsum[LOCAL_THREADS / 32 - 1];
+      int run = (wid > 0 ? (int)S.wsum[wid - 1] : 0) + incl - sum;
 #pragma unroll
-        for (int q = 0; q < LOCAL_PER_THREAD; ++q) {
-          const int i = tid * LOCAL_PER_THREAD + q;
-          if (i < nf) S.pref[i] = (int)run;
-          run += dg[q];
-        }
+      for (int q = 0; q < LOCAL_PER_THREAD; ++q) {
+        const int i = tid * LOCAL_PER_THREAD + q;
+        if (i < ns) S.pref[i] = run;
+        run += dg[q];
       }
     }
-    const bool too_many = E > LOCAL_MAX_EDGES;
-    if (give_back || (lev > 0 && too_many)) {  // hand the level-(k-1) list back
-      if (tid == 0) {
-        S.ctl.list_level = k - 1;
-        S.ctl.list_prev_ok = 1;
-      }
-      local_exit(S, c, il, 1u);
-      return;
-    }
-    if (too_many) {  // first level: the decide kernel never sends this many edges
-      if (tid == 0) {
-        S.ctl.error |= 8;
-        S.ctl.done = 1;
-      }
-      local_exit(S, c, il, 0u);
-      return;
-    }
-    const int nxt = cur ^ 1;
-    unsigned* fbk = d.fb[k & 1];
-    int* gnew = d.qlist[k & 1];
-    for (int i = tid; i < clear_n; i += LOCAL_THREADS) fbk[S.ids[nxt][i] >> 5] = 0u;
-    __syncthreads();  // prefix complete; the level k-2 list consumed
+    __syncthreads();
     // ---- scatter: each thread a contiguous run of at most BATCH edges per pass ----
-    const int Ei = (int)E;
-    for (int e0 = 0; e0 < Ei; e0 += LOCAL_THREADS * BATCH) {
-      const int per = min(BATCH, (Ei - e0 + LOCAL_THREADS - 1) / LOCAL_THREADS);
+    const int* sid = S.sid[p1];
+    for (int e0 = 0; e0 < Es; e0 += LOCAL_THREADS * BATCH) {
+      const int per = min(BATCH, (Es - e0 + LOCAL_THREADS - 1) / LOCAL_THREADS);
       const int ea = e0 + tid * per;
-      const int eb = min(ea + per, Ei);
+      const int eb = min(ea + per, Es);
       int i = 0;
       if (ea < eb) {  // largest i with pref[i] <= ea
-        int lo = 0, hi = nf - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (S.pref[mid] <= ea) lo = mid;
-          else hi = mid - 1;
+        int lo_ = 0, hi_ = ns - 1;
+        while (lo_ < hi_) {
+          const int mid = (lo_ + hi_ + 1) >> 1;
+          if (S.pref[mid] <= ea) lo_ = mid;
+          else hi_ = mid - 1;
         }
-        i = lo;
+        i = lo_;
       }
       int src[BATCH], v[BATCH];
 #pragma unroll
@@ -377,20 +411,19 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) k_push_local(Dev d, IterLaun
         src[q] = -1;
         v[q] = -1;
         if (e < eb) {
-          while (i + 1 < nf && S.pref[i + 1] <= e) ++i;
+          while (i + 1 < ns && S.pref[i + 1] <= e) ++i;
           src[q] = i;
           v[q] = __ldg(d.col + S.base[i] + (long long)(e - S.pref[i]) * C);
         }
       }
-      // values written by this block earlier in the kernel are read past L1
+      // levels, parents and values written during this launch are read past L1
       float fu[BATCH];
 #pragma unroll
       for (int q = 0; q < BATCH; ++q) {
         if (v[q] >= 0 && __ldcg(d.lvl + v[q]) != SS_INF) v[q] = -1;
-        if (SR == SS_REAL) fu[q] = (v[q] >= 0) ? __ldcg(d.fr + S.ids[cur][src[q]]) : 0.0f;
+        if (SR == SS_REAL) fu[q] = (v[q] >= 0) ? __ldcg(d.fr + sid[src[q]]) : 0.0f;
       }
-      // all atomics of the batch in flight before any result is used
-      int old[BATCH];
+      int old[BATCH];  // all atomics of the batch in flight before any result is used
 #pragma unroll
       for (int q = 0; q < BATCH; ++q) {
         old[q] = 0;
@@ -401,34 +434,69 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) k_push_local(Dev d, IterLaun
       }
 #pragma unroll
       for (int q = 0; q < BATCH; ++q) {
-        if (v[q] >= 0 && old[q] < 0) {  // first discoverer appends the vertex
+        if (v[q] >= 0 && old[q] < 0) {  // first discoverer: this CTA owns the vertex
           const int idx = atomicAdd(&S.nnew, 1);
-          gnew[idx] = v[q];
-          if (idx < LOCAL_MAX_FRONTIER) S.ids[nxt][idx] = v[q];
+          if (idx < LOCAL_NEWCAP) {
+            S.nid[idx] = v[q];
+          } else {  // past this CTA's list (skewed slices): the shared overflow list
+            atomicAdd(&S.novf, 1);
+            const unsigned long long o = atomicAdd(d.qovf_n + p0, 1ull);
+            if (o < (unsigned long long)SS_LOCAL_LIST_CAP) d.qovf[o] = v[q];
+            else atomicOr(&S.ctl.error, 16);  // cannot happen: new vertices <= E <= cap
+          }
         }
       }
     }
     __syncthreads();
-    // ---- post: the new level's rows, and their data for the next level ----
-    const int nnew = S.nnew;
+    if (tid < G) {  // tell every CTA how many vertices this one found
+      LocalPub* dst = &cl.map_shared_rank(&S, tid)->all[p0][rank];
+      dst->nsm = min(S.nnew, LOCAL_NEWCAP);
+      dst->novf = S.novf;
+    }
+    if (rank == 0 && tid == 0) d.qovf_n[p1] = 0ull;  // the next level's overflow counter
+    cl.sync();  // #1: every scatter is done, so parents and sums are final
+    // ---- list positions: this CTA's list, then its share of the overflow list ----
+    if (wid == 0) {
+      const int nr = lane < G ? S.all[p0][lane].nsm : 0;
+      const int vr = lane < G ? S.all[p0][lane].novf : 0;
+      const long long novf = __reduce_add_sync(SS_FULL_MASK, (unsigned)vr);
+      long long cntr = nr + (lane < G ? share(novf, lane + 1, G) - share(novf, lane, G) : 0);
+      long long incl = cntr;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const long long t = __shfl_up_sync(SS_FULL_MASK, incl, o);
+        if (lane >= o) incl += t;
+      }
+      if (lane == rank) S.off = incl - cntr;
+      if (lane == 31) S.wsum[0] = incl;  // all new vertices
+      if (lane == 0) S.wsum[1] = novf;
+    }
+    __syncthreads();
+    const long long tot = S.wsum[0], novf = S.wsum[1], off = S.off;
+    const int nsm = S.all[p0][rank].nsm;
+    const long long olo = share(novf, rank, G);
+    const int cnt = nsm + (int)(share(novf, rank + 1, G) - olo);
+    const bool next_here = local_fits(d, (unsigned long long)tot, 0ull);  // next slices fit
+    // ---- post: level, parent, value, frontier bit and list record of each new vertex;
+    // its data also goes straight to the CTA that takes it in the next level ----
     unsigned long long nd = 0;
     unsigned md = 0;
-    for (int i0 = 0; i0 < nnew; i0 += 4 * LOCAL_THREADS) {
+    for (int i0 = 0; i0 < cnt; i0 += 4 * LOCAL_THREADS) {
       int vv[4], pb[4], dv[4], og[4];
-      long long cs[4];
+      long long csv[4];
       float fv[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int i = i0 + q * LOCAL_THREADS + tid;
         vv[q] = -1;
-        if (i < nnew) vv[q] = (i < LOCAL_MAX_FRONTIER) ? S.ids[nxt][i] : __ldcg(gnew + i);
+        if (i < cnt) vv[q] = (i < nsm) ? S.nid[i] : __ldcg(d.qovf + olo + (i - nsm));
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {  // every load of the batch before any store
         if (vv[q] >= 0) {
           pb[q] = __ldcg(d.pbest + vv[q]);
           dv[q] = __ldg(d.rdeg + vv[q]);
-          cs[q] = __ldg(d.cs + vv[q] / C);
+          csv[q] = __ldg(d.cs + vv[q] / C);
           og[q] = __ldg(d.perm + vv[q]);
           fv[q] = (SR == SS_REAL) ? __ldcg(d.psum + vv[q]) : 0.0f;
         }
@@ -445,14 +513,23 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) k_push_local(Dev d, IterLaun
           d.psum[x] = 0.0f;
         }
         atomicOr(fbk + (x >> 5), 1u << (x & 31));
+        const long long at = off + i0 + q * LOCAL_THREADS + tid;
+        const long long bx = csv[q] + (x % C);
+        d.qlist[p0][at] = x;
+        d.qdeg[p0][at] = dv[q];
+        d.qbase[p0][at] = bx;
+        d.qorig[p0][at] = og[q];
+        if (next_here) {
+          const int r = share_owner(at, tot, G);
+          const int slot = (int)(at - share(tot, r, G));
+          LocalSmem* R = cl.map_shared_rank(&S, r);
+          R->sid[p0][slot] = x;
+          R->pref[slot] = dv[q];
+          R->base[slot] = bx;
+          R->orig[slot] = og[q];
+        }
         nd += (unsigned long long)dv[q];
         md = max(md, (unsigned)dv[q]);
-        const int i = i0 + q * LOCAL_THREADS + tid;
-        if (i < LOCAL_MAX_FRONTIER) {
-          S.pref[i] = dv[q];
-          S.base[i] = cs[q] + (x % C);
-          S.orig[i] = og[q];
-        }
       }
     }
 #pragma unroll
@@ -463,44 +540,120 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) k_push_local(Dev d, IterLaun
       S.redmax[wid] = md;
     }
     __syncthreads();
-    if (tid == 0) {
-      unsigned long long td = 0;
-      unsigned tm = 0;
-      for (int w = 0; w < LOCAL_THREADS / 32; ++w) {
-        td += S.red[w];
-        tm = max(tm, S.redmax[w]);
+    if (wid == 0) {
+      unsigned long long td = S.red[lane];
+      unsigned tm = S.redmax[lane];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) td += __shfl_down_sync(SS_FULL_MASK, td, o);
+      tm = __reduce_max_sync(SS_FULL_MASK, tm);
+      td = __shfl_sync(SS_FULL_MASK, td, 0);
+      if (lane < G) {  // tell every CTA this CTA's statistics
+        LocalPub* dst = &cl.map_shared_rank(&S, lane)->all[p0][rank];
+        dst->nd = td;
+        dst->md = tm;
       }
-      S.ctl.qlen[k & 1] = (unsigned long long)nnew;
-      const bool stop = advance_level(d, &S.ctl, k, (unsigned long long)nnew, td,
-                                      (unsigned long long)E, 0ull, tm, VAR_PUSH_LOCAL);
-      S.ctl.list_level = k;
-      S.ctl.list_prev_ok = 1;
-      S.stop = stop ? 1 : 0;
+    }
+    cl.sync();  // #2: every record, slice and statistic of level k is in place
+    if (wid == 0) {
+      unsigned long long td = lane < G ? S.all[p0][lane].nd : 0ull;
+      unsigned tm = lane < G ? S.all[p0][lane].md : 0u;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) td += __shfl_down_sync(SS_FULL_MASK, td, o);
+      tm = __reduce_max_sync(SS_FULL_MASK, tm);
+      if (lane == 0) {
+        S.ctl.qlen[p0] = (unsigned long long)tot;
+        const bool stop = advance_level(d, &S.ctl, k, (unsigned long long)tot, td, (unsigned long long)E,
+                                        0ull, tm, VAR_PUSH_LOCAL, rank == 0);
+        S.ctl.list_level = k;
+        S.ctl.list_prev_ok = 1;
+        S.stop = stop ? 1 : 0;
+        S.red[0] = td;
+      }
     }
     __syncthreads();
     if (S.stop) {
-      local_exit(S, c, il, 0u);
+      local_exit(S, c, il, 0u, cl);
       return;
     }
-    clear_n = nf;  // level k-1 is level (k+1)-2
-    nf = nnew;
-    cur = nxt;
+    if (!next_here) {  // the next frontier does not fit: hand back before using it
+      nf = tot;
+      E = (long long)S.red[0];
+      ++k;
+      if (tid == 0) {
+        S.ctl.list_level = k - 1;
+        S.ctl.list_prev_ok = 1;
+      }
+      local_exit(S, c, il, 1u, cl);
+      return;
+    }
+    ns_prev = ns;  // this level's frontier is level (k+1)-2
+    nf = tot;
+    E = (long long)S.red[0];
     ++k;
   }
+}
+
+static int g_local_cluster[64];  // per device: 0 unknown, -1 none fits, else CTAs per cluster
+
+int push_local_cluster_size() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  if (g_local_cluster[dev] != 0) return g_local_cluster[dev] > 0 ? g_local_cluster[dev] : 0;
+  int best = -1;
+  for (int G : {SS_LOCAL_CLUSTER_MAX, 8}) {
+    auto kern = k_push_local<SS_TROPICAL, 32>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(LocalSmem)) !=
+        cudaSuccess)
+      break;
+    if (G > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+      continue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(G);
+    cfg.blockDim = dim3(LOCAL_THREADS);
+    cfg.dynamicSmemBytes = sizeof(LocalSmem);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = G;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) == cudaSuccess && nclusters >= 1) {
+      best = G;
+      break;
+    }
+  }
+  cudaGetLastError();  // a refused size is not an error of a later call
+  g_local_cluster[dev] = best;
+  return best > 0 ? best : 0;
 }
 
 template <int SR, int C>
 static ss_status launch_push_local_c(const slimsell_graph* h, const Dev& d, const IterLaunch& il,
                                      int max_levels, cudaStream_t st) {
   static bool configured = false;
+  auto kern = k_push_local<SR, C>;
   if (!configured) {
-    SS_CUDA(cudaFuncSetAttribute(k_push_local<SR, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(LocalSmem)));
+    SS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(LocalSmem)));
+    SS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     configured = true;
   }
   k_push_local_prep<<<vertex_grid(h, 32 * PUSH_THREADS), PUSH_THREADS, 0, st>>>(d);
-  k_push_local<SR, C><<<1, LOCAL_THREADS, sizeof(LocalSmem), st>>>(d, il, max_levels);
   SS_CUDA(cudaGetLastError());
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(d.local_cluster);
+  cfg.blockDim = dim3(LOCAL_THREADS);
+  cfg.dynamicSmemBytes = sizeof(LocalSmem);
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = d.local_cluster;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  SS_CUDA(cudaLaunchKernelEx(&cfg, kern, d, il, max_levels));
   return SS_OK;
 }
 

@@ -60,9 +60,8 @@ __device__ int heuristic_variant(const Dev& d, const Ctl* c) {
   const unsigned long long nf = c->prev_new, mf = c->prev_deg;
   const unsigned long long mu = (unsigned long long)d.nnz - c->reached_deg;
   if (c->prev_variant < 0) return VAR_PUSH;
-  // a frontier the single-block push takes is cheaper there than in any grid-wide pass
-  if (nf <= (unsigned long long)LOCAL_MAX_FRONTIER && mf <= (unsigned long long)LOCAL_MAX_EDGES)
-    return VAR_PUSH;
+  // a frontier the cluster push takes is cheaper there than in any grid-wide pass
+  if (local_fits(d, nf, mf)) return VAR_PUSH;
   if (c->prev_variant == VAR_PUSH || c->prev_variant == VAR_PUSH_LOCAL) return (14ull * mf > mu) ? VAR_FILTERED : VAR_PUSH;
   const bool shrinking = c->prev_new < c->prev2_new;
   return (24ull * nf < (unsigned long long)d.n && shrinking) ? VAR_PUSH : VAR_FILTERED;
@@ -145,10 +144,8 @@ __global__ void k_decide(Dev d, int policy, cudaGraphConditionalHandle sw, int u
   if (t == 0) {
     int v = choice;
     if (v == VAR_PUSH && !push_fits(d, c)) v = VAR_FILTERED;
-    // small frontiers go to the single-block push (several levels per launch)
-    if (v == VAR_PUSH && c->prev_new <= (unsigned long long)LOCAL_MAX_FRONTIER &&
-        c->prev_deg <= (unsigned long long)LOCAL_MAX_EDGES)
-      v = VAR_PUSH_LOCAL;
+    // small frontiers go to the cluster push (several levels per launch)
+    if (v == VAR_PUSH && local_fits(d, c->prev_new, c->prev_deg)) v = VAR_PUSH_LOCAL;
     c->variant = v;
     if (use_sw) cudaGraphSetConditional(sw, (unsigned)v);
   }

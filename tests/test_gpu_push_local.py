@@ -1,9 +1,9 @@
-"""GPU parity of the single-block push: small frontiers (at most 8192 vertices
-and 65536 edges) run level after level inside one 1024-thread block, with the
-frontier kept as a vertex list, and hand back to the grid-wide variants when a
-level outgrows the block.  Results must equal the oracle's bit for bit, for
-every semiring, in the device-side and the host-driven loop, across hand-overs
-in both directions.
+"""GPU parity of the cluster push: small frontiers (at most 4096 vertices and
+8192 edges per CTA of a 16- or 8-CTA thread-block cluster) run level after
+level inside one launch, with the frontier kept as a vertex list, and hand back
+to the grid-wide variants when a level outgrows the cluster.  Results must equal
+the oracle's bit for bit, for every semiring, in the device-side and the
+host-driven loop, across hand-overs in both directions.
 """
 import numpy as np
 import pytest
@@ -36,7 +36,7 @@ def path_graph(n, seed=1):
     return relabelled(n, [(i, i + 1) for i in range(n - 1)], seed, f"path{n}")
 
 
-def grow_shrink(tail=300, fan=10000, seed=2):
+def grow_shrink(tail=300, fan=70000, seed=2):
     """path -- hub -- fan leaves -- hub -- path: a level of `fan` vertices between
     two long runs of one-vertex levels."""
     e, v = [], 0
@@ -55,7 +55,7 @@ def grow_shrink(tail=300, fan=10000, seed=2):
     return relabelled(v + 1, e, seed, f"growshrink{tail}-{fan}")
 
 
-def wide_star(tail=200, leaves=70000, seed=3):
+def wide_star(tail=200, leaves=140000, seed=3):
     """A path ending in a hub whose degree alone exceeds the block's edge budget."""
     e = [(i, i + 1) for i in range(tail)]
     hub = tail
@@ -108,7 +108,7 @@ def test_hand_over_both_ways(policy, loop):
         for sr in SEMIRINGS:
             seq = check(G, g, r, sr, policy)
             if policy != "learned":
-                i = seq.index(next(v for v in seq if v != LOCAL))  # the wide level left the block
+                i = seq.index(next(v for v in seq if v != LOCAL))  # the wide level left the cluster
                 assert LOCAL in seq[:i] and LOCAL in seq[i + 1:], seq
     G.close()
 
@@ -122,7 +122,7 @@ def test_edge_budget_hand_back(loop):
     for sr in SEMIRINGS:
         for policy in ["push", "heuristic"]:
             seq = check(G, g, r, sr, policy)
-            assert seq[0] == LOCAL and seq[-1] != LOCAL, seq  # the hub's 70001 edges
+            assert seq[0] == LOCAL and seq[-1] != LOCAL, seq  # the hub's 140001 edges
     G.close()
 
 
@@ -143,9 +143,9 @@ def test_sparse_families_device_vs_host_loop(maker):
 def test_alternating_policies_keep_scratch_clean():
     """Pull, single-block push and grid push share the frontier bitmaps and push
     scratch; alternating runs on one handle must not leak state between runs."""
-    g, p = grow_shrink(tail=120, fan=9000, seed=7)
+    g, p = grow_shrink(tail=120, fan=66000, seed=7)
     G = ss.SlimSellGraph.from_host(g.row_ptr, g.col, C=32, sigma=g.n, split_w=256)
-    roots = [int(p[0]), int(p[130]), int(p[9200]), int(p[60])]
+    roots = [int(p[0]), int(p[130]), int(p[66200]), int(p[60])]
     for i, r in enumerate(roots * 2):
         for pol in ["slimwork", "push", "pull_filtered", "heuristic"][i % 4:] + ["full"]:
             check(G, g, r, SEMIRINGS[i % 4], pol)
