@@ -134,6 +134,10 @@ __device__ __forceinline__ void post_chunk(const Dev& d, int k, int chunk, int l
           if (SR == SS_REAL) d.fr[R0 + r] = a.sum[r];
         }
       *reinterpret_cast<int4*>(d.lvl + R0) = make_int4(L[0], L[1], L[2], L[3]);
+      // the push variants tell visited vertices apart by their pbest slot
+      *reinterpret_cast<int4*>(d.pbest + R0) =
+          make_int4(L[0] == SS_INF ? -1 : SS_PBEST_VISITED, L[1] == SS_INF ? -1 : SS_PBEST_VISITED,
+                    L[2] == SS_INF ? -1 : SS_PBEST_VISITED, L[3] == SS_INF ? -1 : SS_PBEST_VISITED);
       const int4 dg = *reinterpret_cast<const int4*>(d.rdeg + R0);
       const int D[4] = {dg.x, dg.y, dg.z, dg.w};
 #pragma unroll
@@ -376,11 +380,9 @@ __global__ void k_init(Dev d) {
     d.xacc[s] = 0.0f;
     d.xpar[s] = -1;
   }
-  if (d.ctl->error) {  // a previous run stopped early: restore the push scratch invariants
-    for (long long r = t0; r < d.n_pad; r += stride) {
-      d.pbest[r] = -1;
-      d.psum[r] = 0.0f;
-    }
+  for (long long r = t0; r < d.n_pad; r += stride) d.pbest[r] = -1;  // nothing visited
+  if (d.ctl->error) {  // a previous run stopped early: restore the push scratch invariant
+    for (long long r = t0; r < d.n_pad; r += stride) d.psum[r] = 0.0f;
   }
 }
 

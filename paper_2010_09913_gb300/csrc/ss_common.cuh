@@ -13,6 +13,7 @@
 #define SS_INF 0x7fffffff          // tropical infinity / "unvisited" level
 #define SS_PAD_LEVEL (-1)          // level of padding rows (never unvisited, never in a frontier)
 #define SS_FULL_MASK 0xffffffffu
+#define SS_PBEST_VISITED 0x7fffffff  // pbest of a visited vertex (above every original id)
 #define SS_SMEM_MAX_BYTES 212992   // frontier-bitmap prefix staged per block (1,703,936 vertices)
 #define SS_SMEM_LIMIT_BYTES 214016 // dynamic shared memory requested at most (prefix + guard)
 // cluster push: frontier entries and frontier edges per CTA, largest cluster, list capacity
@@ -87,7 +88,8 @@ struct Dev {
   unsigned* arrive;     // [n_split] SlimChunk arrival counters
   int2* units;          // [units_cap] push work units (row, first neighbour index)
   long long units_cap;
-  int* pbest;           // [n_pad] push: largest frontier-neighbour original id (-1 = none)
+  int* pbest;           // [n_pad] push: largest frontier-neighbour original id (-1 = none yet,
+                        // SS_PBEST_VISITED once the vertex has a level)
   float* psum;          // [n_pad] push: real-semiring sum of frontier-neighbour values
   unsigned* touched;    // [fb_words] push: rows reached by the current push
   int* qlist[2];        // [n_pad] vertex lists of a level (cluster push), by parity

@@ -144,6 +144,7 @@ __device__ __forceinline__ void finish_iteration_block(const Dev& d, unsigned lo
 __device__ __forceinline__ void init_root_state(const Dev& d, int root) {
   const int r = d.invperm[root];
   d.lvl[r] = 0;
+  d.pbest[r] = SS_PBEST_VISITED;
   d.fb[0][r >> 5] |= 1u << (r & 31);
   d.fr[r] = 1.0f;
   d.par[r] = root + 1;

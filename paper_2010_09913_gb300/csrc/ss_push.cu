@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(PUSH_THREADS) k_push_post(Dev d, IterLaunch il
       const int v = (int)(w * 32 + b);
       d.lvl[v] = k;
       d.par[v] = d.pbest[v] + 1;  // largest-id frontier neighbour + 1
-      d.pbest[v] = -1;
+      d.pbest[v] = SS_PBEST_VISITED;
       if (SR == SS_REAL) {
         d.fr[v] = d.psum[v];
         d.psum[v] = 0.0f;
@@ -183,6 +183,7 @@ __global__ void __launch_bounds__(PUSH_THREADS) k_push_post(Dev d, IterLaunch il
 constexpr int LOCAL_THREADS = 1024;
 constexpr int LOCAL_BATCH = 16;     // candidate edges per thread in flight
 constexpr int LOCAL_NEWCAP = 8192;  // new vertices per CTA kept in shared memory
+constexpr int LOCAL_POST = 2;       // new vertices per thread in flight in the post step
 constexpr int LOCAL_PER_THREAD = SS_LOCAL_SLICE / LOCAL_THREADS;
 constexpr int CTL_WORDS = (int)(sizeof(Ctl) / sizeof(unsigned));
 static_assert(sizeof(Ctl) % sizeof(unsigned) == 0, "control block copied as words");
@@ -191,7 +192,7 @@ static_assert(SS_LOCAL_SLICE % LOCAL_THREADS == 0, "whole frontier entries per t
 struct LocalPub {             // what each CTA tells every CTA of the cluster about a level
   int nsm;                    // new vertices it holds in shared memory
   int novf;                   // new vertices it put in the overflow list
-  unsigned md;                // largest degree of its new vertices
+  unsigned md;                // largest degree of the vertices it posted
   unsigned long long nd;      // their degree sum
 };
 
@@ -206,8 +207,7 @@ struct LocalSmem {
   unsigned long long red[LOCAL_THREADS / 32];
   unsigned redmax[LOCAL_THREADS / 32];
   LocalPub all[2][SS_LOCAL_CLUSTER_MAX];  // written by every CTA of the cluster, by level parity
-  long long off;                       // first list position of this CTA's new vertices
-  int nnew, novf, stop;
+  int nnew, novf, es;
 };
 static_assert(sizeof(LocalSmem) <= 227 * 1024, "cluster push shared memory");
 
@@ -264,14 +264,18 @@ __device__ __forceinline__ void local_exit(LocalSmem& S, Ctl* c, const IterLaunc
 
 extern __shared__ __align__(16) unsigned char ss_local_smem[];
 
-// CTA r's first entry of a list of `total` entries split into G equal shares.
-__device__ __forceinline__ long long share(long long total, int r, int G) { return total * r / G; }
+// CTA r's first entry of a list of `total` entries split into G = 2^lg equal
+// shares (every list here has fewer than 2^27 entries, so 32 bits hold total * G).
+__device__ __forceinline__ long long share(long long total, int r, int lg) {
+  return (long long)(((unsigned)total * (unsigned)r) >> lg);
+}
 
 // The CTA whose share holds list entry `at` (0 <= at < total).
-__device__ __forceinline__ int share_owner(long long at, long long total, int G) {
-  int r = (int)((at * G) / total);
-  while (r + 1 < G && share(total, r + 1, G) <= at) ++r;
-  while (r > 0 && share(total, r, G) > at) --r;
+__device__ __forceinline__ int share_owner(long long at, long long total, int lg) {
+  const int G = 1 << lg;
+  int r = (int)(((unsigned)at << lg) / (unsigned)total);
+  while (r + 1 < G && share(total, r + 1, lg) <= at) ++r;
+  while (r > 0 && share(total, r, lg) > at) --r;
   return r;
 }
 
@@ -280,7 +284,8 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) k_push_local(Dev d, IterLaun
   constexpr int BATCH = (SR == SS_REAL) ? LOCAL_BATCH / 2 : LOCAL_BATCH;  // registers
   LocalSmem& S = *reinterpret_cast<LocalSmem*>(ss_local_smem);
   cg::cluster_group cl = cg::this_cluster();
-  const int G = (int)cl.num_blocks();
+  const int G = (int)cl.num_blocks();  // 8 or 16
+  const int lg = 31 - __clz(G);
   const int rank = (int)cl.block_rank();
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   Ctl* c = d.ctl;
@@ -311,8 +316,8 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) k_push_local(Dev d, IterLaun
   // left; later slices arrive in shared memory from the CTAs that found them
   {
     const int p1 = (k - 1) & 1;
-    const long long lo = share(nf, rank, G);
-    const int ns = (int)(share(nf, rank + 1, G) - lo);
+    const long long lo = share(nf, rank, lg);
+    const int ns = (int)(share(nf, rank + 1, lg) - lo);
     for (int i = tid; i < ns; i += LOCAL_THREADS) {
       const int u = __ldcg(d.qlist[p1] + lo + i);
       S.sid[p1][i] = u;
@@ -327,11 +332,13 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) k_push_local(Dev d, IterLaun
       }
     }
     const long long n2 = (have_list && S.ctl.list_prev_ok) ? (long long)S.ctl.qlen[k & 1] : 0;
-    const long long lo2 = share(n2, rank, G), hi2 = share(n2, rank + 1, G);
+    const long long lo2 = share(n2, rank, lg), hi2 = share(n2, rank + 1, lg);
     unsigned* fbk = d.fb[k & 1];
     for (long long i = lo2 + tid; i < hi2; i += LOCAL_THREADS) fbk[__ldcg(d.qlist[k & 1] + i) >> 5] = 0u;
   }
+  __syncthreads();  // the first slice is in place
   int ns_prev = 0;  // entries of S.sid[k&1]: this CTA's slice of level k-2 (after the first level)
+  unsigned long long reached = S.ctl.reached;  // every thread tracks the stop condition
   for (int lev = 0;; ++lev) {
     if (lev > 0 && (lev >= max_levels || !local_fits(d, (unsigned long long)nf, (unsigned long long)E))) {
       if (tid == 0) {  // hand the level-(k-1) list back
@@ -343,22 +350,44 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) k_push_local(Dev d, IterLaun
     }
     const int p1 = (k - 1) & 1, p0 = k & 1;
     unsigned* fbk = d.fb[p0];
-    const int ns = (int)(share(nf, rank + 1, G) - share(nf, rank, G));
+    const int ns = (int)(share(nf, rank + 1, lg) - share(nf, rank, lg));
     for (int i = tid; i < ns_prev; i += LOCAL_THREADS) fbk[S.sid[p0][i] >> 5] = 0u;  // level k-2
     if (tid == 0) {
       S.nnew = 0;
       S.novf = 0;
     }
-    __syncthreads();
-    // ---- exclusive prefix of the slice's degrees, in place ----
-    int Es;
-    {
+    // ---- exclusive prefix of the slice's degrees, in place (slice edges <= E <= d.local_max_e) ----
+    if (ns <= 8 * 32) {  // small slice: one warp
+      if (wid == 0) {
+        int dg[8], sum = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int i = lane * 8 + q;
+          dg[q] = (i < ns) ? S.pref[i] : 0;
+          sum += dg[q];
+        }
+        int incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int t = __shfl_up_sync(SS_FULL_MASK, incl, o);
+          if (lane >= o) incl += t;
+        }
+        int run = incl - sum;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int i = lane * 8 + q;
+          if (i < ns) S.pref[i] = run;
+          run += dg[q];
+        }
+        if (lane == 31) S.es = incl;
+      }
+    } else {
       int dg[LOCAL_PER_THREAD], sum = 0;
 #pragma unroll
       for (int q = 0; q < LOCAL_PER_THREAD; ++q) {
         const int i = tid * LOCAL_PER_THREAD + q;
         dg[q] = (i < ns) ? S.pref[i] : 0;
-        sum += dg[q];  // the slice's edges are at most E <= d.local_max_e
+        sum += dg[q];
       }
       int incl = sum;
 #pragma unroll
@@ -378,7 +407,6 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) k_push_local(Dev d, IterLaun
         S.wsum[lane] = w;
       }
       __syncthreads();
-      Es = (int)S.wsum[LOCAL_THREADS / 32 - 1];
       int run = (wid > 0 ? (int)S.wsum[wid - 1] : 0) + incl - sum;
 #pragma unroll
       for (int q = 0; q < LOCAL_PER_THREAD; ++q) {
@@ -386,8 +414,10 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) k_push_local(Dev d, IterLaun
         if (i < ns) S.pref[i] = run;
         run += dg[q];
       }
+      if (tid == LOCAL_THREADS - 1) S.es = (int)S.wsum[LOCAL_THREADS / 32 - 1];
     }
     __syncthreads();
+    const int Es = S.es;
     // ---- scatter: each thread a contiguous run of at most BATCH edges per pass ----
     const int* sid = S.sid[p1];
     for (int e0 = 0; e0 < Es; e0 += LOCAL_THREADS * BATCH) {
@@ -416,25 +446,23 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) k_push_local(Dev d, IterLaun
           v[q] = __ldg(d.col + S.base[i] + (long long)(e - S.pref[i]) * C);
         }
       }
-      // levels, parents and values written during this launch are read past L1
-      float fu[BATCH];
+      // one atomicMax per candidate claims it, finds the largest-id parent and
+      // tells visited vertices apart (their slot holds SS_PBEST_VISITED, which no
+      // id exceeds); all atomics of the batch are in flight before a result is used
+      int old[BATCH];
 #pragma unroll
       for (int q = 0; q < BATCH; ++q) {
-        if (v[q] >= 0 && __ldcg(d.lvl + v[q]) != SS_INF) v[q] = -1;
-        if (SR == SS_REAL) fu[q] = (v[q] >= 0) ? __ldcg(d.fr + sid[src[q]]) : 0.0f;
+        old[q] = SS_PBEST_VISITED;
+        if (v[q] >= 0) old[q] = atomicMax(d.pbest + v[q], S.orig[src[q]]);
       }
-      int old[BATCH];  // all atomics of the batch in flight before any result is used
+      if (SR == SS_REAL) {  // values of this launch's vertices are read past L1
 #pragma unroll
-      for (int q = 0; q < BATCH; ++q) {
-        old[q] = 0;
-        if (v[q] >= 0) {
-          if (SR == SS_REAL) atomicAdd(d.psum + v[q], fu[q]);
-          old[q] = atomicMax(d.pbest + v[q], S.orig[src[q]]);
-        }
+        for (int q = 0; q < BATCH; ++q)
+          if (old[q] != SS_PBEST_VISITED) atomicAdd(d.psum + v[q], __ldcg(d.fr + sid[src[q]]));
       }
 #pragma unroll
       for (int q = 0; q < BATCH; ++q) {
-        if (v[q] >= 0 && old[q] < 0) {  // first discoverer: this CTA owns the vertex
+        if (old[q] < 0) {  // first discoverer: this CTA owns the vertex
           const int idx = atomicAdd(&S.nnew, 1);
           if (idx < LOCAL_NEWCAP) {
             S.nid[idx] = v[q];
@@ -455,44 +483,42 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) k_push_local(Dev d, IterLaun
     }
     if (rank == 0 && tid == 0) d.qovf_n[p1] = 0ull;  // the next level's overflow counter
     cl.sync();  // #1: every scatter is done, so parents and sums are final
-    // ---- list positions: this CTA's list, then its share of the overflow list ----
-    if (wid == 0) {
+    // ---- list positions (every warp alike): this CTA's list, then its share of the overflow ----
+    long long tot, novf, off;
+    {
       const int nr = lane < G ? S.all[p0][lane].nsm : 0;
       const int vr = lane < G ? S.all[p0][lane].novf : 0;
-      const long long novf = __reduce_add_sync(SS_FULL_MASK, (unsigned)vr);
-      long long cntr = nr + (lane < G ? share(novf, lane + 1, G) - share(novf, lane, G) : 0);
+      novf = (long long)__reduce_add_sync(SS_FULL_MASK, (unsigned)vr);
+      const long long cntr = nr + (lane < G ? share(novf, lane + 1, lg) - share(novf, lane, lg) : 0);
       long long incl = cntr;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const long long t = __shfl_up_sync(SS_FULL_MASK, incl, o);
         if (lane >= o) incl += t;
       }
-      if (lane == rank) S.off = incl - cntr;
-      if (lane == 31) S.wsum[0] = incl;  // all new vertices
-      if (lane == 0) S.wsum[1] = novf;
+      tot = __shfl_sync(SS_FULL_MASK, incl, 31);
+      off = __shfl_sync(SS_FULL_MASK, incl - cntr, rank);
     }
-    __syncthreads();
-    const long long tot = S.wsum[0], novf = S.wsum[1], off = S.off;
     const int nsm = S.all[p0][rank].nsm;
-    const long long olo = share(novf, rank, G);
-    const int cnt = nsm + (int)(share(novf, rank + 1, G) - olo);
+    const long long olo = share(novf, rank, lg);
+    const int cnt = nsm + (int)(share(novf, rank + 1, lg) - olo);
     const bool next_here = local_fits(d, (unsigned long long)tot, 0ull);  // next slices fit
     // ---- post: level, parent, value, frontier bit and list record of each new vertex;
     // its data also goes straight to the CTA that takes it in the next level ----
     unsigned long long nd = 0;
     unsigned md = 0;
-    for (int i0 = 0; i0 < cnt; i0 += 4 * LOCAL_THREADS) {
-      int vv[4], pb[4], dv[4], og[4];
-      long long csv[4];
-      float fv[4];
+    for (int i0 = 0; i0 < cnt; i0 += LOCAL_POST * LOCAL_THREADS) {
+      int vv[LOCAL_POST], pb[LOCAL_POST], dv[LOCAL_POST], og[LOCAL_POST];
+      long long csv[LOCAL_POST];
+      float fv[LOCAL_POST];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < LOCAL_POST; ++q) {
         const int i = i0 + q * LOCAL_THREADS + tid;
         vv[q] = -1;
         if (i < cnt) vv[q] = (i < nsm) ? S.nid[i] : __ldcg(d.qovf + olo + (i - nsm));
       }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {  // every load of the batch before any store
+      for (int q = 0; q < LOCAL_POST; ++q) {  // every load of the batch before any store
         if (vv[q] >= 0) {
           pb[q] = __ldcg(d.pbest + vv[q]);
           dv[q] = __ldg(d.rdeg + vv[q]);
@@ -502,12 +528,12 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) k_push_local(Dev d, IterLaun
         }
       }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < LOCAL_POST; ++q) {
         if (vv[q] < 0) continue;
         const int x = vv[q];
         d.lvl[x] = k;
         d.par[x] = pb[q] + 1;  // largest-id frontier neighbour + 1
-        d.pbest[x] = -1;
+        d.pbest[x] = SS_PBEST_VISITED;
         if (SR == SS_REAL) {
           d.fr[x] = fv[q];
           d.psum[x] = 0.0f;
@@ -520,8 +546,8 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) k_push_local(Dev d, IterLaun
         d.qbase[p0][at] = bx;
         d.qorig[p0][at] = og[q];
         if (next_here) {
-          const int r = share_owner(at, tot, G);
-          const int slot = (int)(at - share(tot, r, G));
+          const int r = share_owner(at, tot, lg);
+          const int slot = (int)(at - share(tot, r, lg));
           LocalSmem* R = cl.map_shared_rank(&S, r);
           R->sid[p0][slot] = x;
           R->pref[slot] = dv[q];
@@ -532,6 +558,7 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) k_push_local(Dev d, IterLaun
         md = max(md, (unsigned)dv[q]);
       }
     }
+    // this CTA's statistics, told to every CTA
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) nd += __shfl_down_sync(SS_FULL_MASK, nd, o);
     md = __reduce_max_sync(SS_FULL_MASK, md);
@@ -541,43 +568,39 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) k_push_local(Dev d, IterLaun
     }
     __syncthreads();
     if (wid == 0) {
-      unsigned long long td = S.red[lane];
-      unsigned tm = S.redmax[lane];
+      unsigned long long w = S.red[lane];
+      unsigned m = S.redmax[lane];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) td += __shfl_down_sync(SS_FULL_MASK, td, o);
-      tm = __reduce_max_sync(SS_FULL_MASK, tm);
-      td = __shfl_sync(SS_FULL_MASK, td, 0);
-      if (lane < G) {  // tell every CTA this CTA's statistics
+      for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(SS_FULL_MASK, w, o);
+      m = __reduce_max_sync(SS_FULL_MASK, m);
+      if (lane < G) {
         LocalPub* dst = &cl.map_shared_rank(&S, lane)->all[p0][rank];
-        dst->nd = td;
-        dst->md = tm;
+        dst->nd = w;
+        dst->md = m;
       }
     }
     cl.sync();  // #2: every record, slice and statistic of level k is in place
-    if (wid == 0) {
-      unsigned long long td = lane < G ? S.all[p0][lane].nd : 0ull;
-      unsigned tm = lane < G ? S.all[p0][lane].md : 0u;
+    // ---- totals (every warp alike) and the stop decision ----
+    unsigned long long td = lane < G ? S.all[p0][lane].nd : 0ull;
+    unsigned tm = lane < G ? S.all[p0][lane].md : 0u;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) td += __shfl_down_sync(SS_FULL_MASK, td, o);
-      tm = __reduce_max_sync(SS_FULL_MASK, tm);
-      if (lane == 0) {
-        S.ctl.qlen[p0] = (unsigned long long)tot;
-        const bool stop = advance_level(d, &S.ctl, k, (unsigned long long)tot, td, (unsigned long long)E,
-                                        0ull, tm, VAR_PUSH_LOCAL, rank == 0);
-        S.ctl.list_level = k;
-        S.ctl.list_prev_ok = 1;
-        S.stop = stop ? 1 : 0;
-        S.red[0] = td;
-      }
+    for (int o = 16; o > 0; o >>= 1) td += __shfl_xor_sync(SS_FULL_MASK, td, o);
+    tm = __reduce_max_sync(SS_FULL_MASK, tm);
+    reached += (unsigned long long)tot;
+    // the same decision advance_level takes on the control block
+    const bool stop = tot == 0 || k >= d.n + 1 || reached > d.reach_cap;
+    if (tid == 0) {
+      S.ctl.qlen[p0] = (unsigned long long)tot;
+      advance_level(d, &S.ctl, k, (unsigned long long)tot, td, (unsigned long long)E, 0ull, tm,
+                    VAR_PUSH_LOCAL, rank == 0);
+      S.ctl.list_level = k;
+      S.ctl.list_prev_ok = 1;
     }
-    __syncthreads();
-    if (S.stop) {
+    if (stop) {
       local_exit(S, c, il, 0u, cl);
       return;
     }
     if (!next_here) {  // the next frontier does not fit: hand back before using it
-      nf = tot;
-      E = (long long)S.red[0];
       ++k;
       if (tid == 0) {
         S.ctl.list_level = k - 1;
@@ -588,10 +611,11 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) k_push_local(Dev d, IterLaun
     }
     ns_prev = ns;  // this level's frontier is level (k+1)-2
     nf = tot;
-    E = (long long)S.red[0];
+    E = (long long)td;
     ++k;
   }
 }
+
 
 static int g_local_cluster[64];  // per device: 0 unknown, -1 none fits, else CTAs per cluster
 
