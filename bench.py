@@ -401,6 +401,52 @@ def roofline_at_scale(ss, torch, scale, nroots, split_w, stream, dev):
     return out
 
 
+def high_diameter(ss, torch, stream, dev, nroots=16):
+    """High-diameter and low-skew graphs: a 4096 x 4096 lattice with 5% of its
+    edges deleted and an Erdos-Renyi graph (n = 2^22, mean degree 16); sel-max
+    and tropical; C = 32, sigma = N; 16 seeded roots.  The adaptive schedule
+    (frontier-size rule, small levels in the cluster push) next to the plain
+    SlimWork pass, which on the lattice is timed on a 2-root sample (one run
+    takes most of a second there)."""
+    out = {}
+    for name, g in (("lattice 4096^2 (5% deleted)", gg.lattice(4096, 0.05, seed=1)),
+                    ("erdos-renyi 2^22 (mean degree 16)", gg.erdos_renyi(1 << 22, 16.0, seed=1))):
+        roots = gg.roots(g, nroots, seed=2)
+        rp_d = torch.from_numpy(g.row_ptr).to(dev)
+        col_d = torch.from_numpy(g.col).to(dev)
+        h = ss.slimsell_build(rp_d, col_d, g.n, g.nnz, 32, g.n, 256, stream)
+        del rp_d, col_d
+        res = {"n": g.n, "nnz": g.nnz, "roots": nroots}
+        lattice = name.startswith("lattice")
+        for sr in ("selmax", "tropical"):
+            for pol_name, pol, rs in (("heuristic", ss.V_HEURISTIC, roots),
+                                      ("slimwork", ss.V_SLIMWORK, roots[:2] if lattice else roots)):
+                ss.slimsell_bfs(h, int(rs[0]), SR_ID[sr], pol, None, None, stream)  # warm-up
+                edges, iters, local = 0, 0, 0
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                ms = 0.0
+                for r in rs:
+                    torch.cuda.synchronize()
+                    e0.record(stream)
+                    ss.slimsell_bfs(h, int(r), SR_ID[sr], pol, None, None, stream)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ms += e0.elapsed_time(e1)
+                    st, its = ss.slimsell_get_run_stats(h, cap=16384)
+                    edges += st.reached_degree // 2
+                    iters += st.iterations
+                    local += sum(1 for i in range(1, min(st.iterations, 16383) + 1)
+                                 if its[i].variant == ss.VARIANT_PUSH_LOCAL)
+                res[f"{sr}_{pol_name}"] = {"gteps": edges / (ms / 1000.0) / 1e9,
+                                           "ms_per_run": ms / len(rs), "runs": len(rs),
+                                           "levels_per_run": iters / len(rs),
+                                           "cluster_push_levels_per_run": local / len(rs)}
+        ss.slimsell_destroy(h)
+        out[name] = res
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -415,6 +461,7 @@ def main():
     ap.add_argument("--no-ablations", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-scale24", action="store_true")
+    ap.add_argument("--no-high-diameter", action="store_true")
     ap.add_argument("--batch-graphs", type=int, default=200)
     args = ap.parse_args()
     world, rank, local, pg = dist_setup()
@@ -552,6 +599,9 @@ def main():
     if not args.no_scale24 and rank == 0:
         torch.cuda.empty_cache()
         line["scale24"] = roofline_at_scale(ss, torch, 24, 8, args.split_w, stream, dev)
+    if not args.no_high_diameter and rank == 0:
+        torch.cuda.empty_cache()
+        line["high_diameter"] = high_diameter(ss, torch, stream, dev)
     if rank == 0 and world == 1 and not args.no_cpu:
         edges, t_cpu, nruns = cpu_oracle_sample(g, roots, 20.0)
         line["cpu_baseline"] = {"value": edges / t_cpu / 1e9, "unit": "GTEPS", "cores": 1,
