@@ -38,23 +38,56 @@
 
 namespace ss {
 
-constexpr int PULL_THREADS = 1024;  // one block per SM, 32 warps
-constexpr int PULL_STEP = 4;        // int4 col loads in flight per lane (16 slots)
+// Compile-time tunables of the pull kernel (defaults measured best on GB300).
+#ifndef SS_PULL_STEP
+#define SS_PULL_STEP 4
+#endif
+#ifndef SS_PULL_STEP_REAL
+#define SS_PULL_STEP_REAL 3  // the real semiring also gathers a value per hit
+#endif
+#ifndef SS_PULL_PREFETCH
+#define SS_PULL_PREFETCH 0  // bulk L2 prefetch distance beyond the next step (0: next step only)
+#endif
+#ifndef SS_PULL_LOAD
+#define SS_PULL_LOAD 2  // col loads: 0 evict-first, 1 no-L1 with 256-byte L2 fetches, 2 no-L1
+#endif
+
+constexpr int PULL_THREADS = SS_PULL_THREADS;  // one block per SM
+// int4 col loads in flight per lane (4 slots each)
+template <int SR>
+__host__ __device__ constexpr int pull_step() { return SR == SS_REAL ? SS_PULL_STEP_REAL : SS_PULL_STEP; }
 // Stage the bitmap prefix only when the previous iteration read at least this
 // many slots; below it, reading frontier bits from global memory is cheaper.
 constexpr unsigned long long STAGE_MIN_SLOTS = 2ull << 20;
 
 enum { MODE_FULL = 0, MODE_SLIMWORK = 1, MODE_FILTERED = 3 };
 
-__device__ __forceinline__ int4 ld_stream(const int4* p) { return __ldcs(p); }
+__device__ __forceinline__ int4 ld_stream(const int4* p) {
+#if SS_PULL_LOAD == 1
+  int4 v;
+  asm("ld.global.nc.L1::no_allocate.L2::256B.v4.s32 {%0, %1, %2, %3}, [%4];"
+      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+      : "l"(p));
+  return v;
+#elif SS_PULL_LOAD == 2
+  int4 v;
+  asm("ld.global.nc.L1::no_allocate.v4.s32 {%0, %1, %2, %3}, [%4];"
+      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+      : "l"(p));
+  return v;
+#else
+  return __ldcs(p);
+#endif
+}
 
 // Ask the TMA unit to pull [p, p + bytes) into L2 ahead of the warp's loads
 // (p 16-byte aligned, bytes a positive multiple of 16).
 __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+  if (bytes == 0) return;
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
 }
 
-constexpr int PREFETCH_BYTES = 4096;  // col bytes prefetched ahead of each warp
+constexpr int PREFETCH_BYTES = SS_PULL_PREFETCH;  // col bytes prefetched ahead of each warp
 
 __device__ __forceinline__ int4 shfl_int4(int4 v, int src) {
   return make_int4(__shfl_sync(SS_FULL_MASK, v.x, src), __shfl_sync(SS_FULL_MASK, v.y, src),
@@ -196,6 +229,7 @@ template <int SR, int C, int MODE>
 __global__ void __launch_bounds__(PULL_THREADS, 1) k_pull(Dev d, int variant,
                                                           cudaGraphConditionalHandle cond,
                                                           int use_cond) {
+  constexpr int PULL_STEP = pull_step<SR>();
   constexpr int Q = C / 4;
   if (d.ctl->done) return;
   const int k = d.ctl->k;
@@ -395,6 +429,7 @@ __global__ void k_init_root(Dev d, int root) { init_root_state(d, root); }
 template <int C>
 __global__ void __launch_bounds__(PULL_THREADS, 1) k_dp(Dev d) {
   constexpr int Q = C / 4;
+  constexpr int PULL_STEP = SS_PULL_STEP;
   const int lane = threadIdx.x & 31;
   const int wid = blockIdx.x * (PULL_THREADS / 32) + (threadIdx.x >> 5);
   const int nw = gridDim.x * (PULL_THREADS / 32);

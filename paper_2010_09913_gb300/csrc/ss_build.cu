@@ -402,7 +402,7 @@ static ss_status order_items(slimsell_graph* h, cudaStream_t st) {
   std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
     return (items[a].z - items[a].y) * C + overhead > (items[b].z - items[b].y) * C + overhead;
   });
-  const long long W = (long long)h->num_sms * 32;
+  const long long W = (long long)h->num_sms * (SS_PULL_THREADS / 32);
   for (long long p = 0; p < n; ++p) {
     const long long r = p / W, w = p % W;
     const long long round_len = std::min<long long>(W, n - r * W);

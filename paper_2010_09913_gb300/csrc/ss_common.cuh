@@ -16,6 +16,10 @@
 #define SS_PBEST_VISITED 0x7fffffff  // pbest of a visited vertex (above every original id)
 #define SS_SMEM_MAX_BYTES 212992   // frontier-bitmap prefix staged per block (1,703,936 vertices)
 #define SS_SMEM_LIMIT_BYTES 214016 // dynamic shared memory requested at most (prefix + guard)
+// threads of a pull-iteration block (one block per SM); the item order assumes it
+#ifndef SS_PULL_THREADS
+#define SS_PULL_THREADS 1024
+#endif
 // cluster push: frontier entries and frontier edges per CTA, largest cluster, list capacity
 #define SS_LOCAL_SLICE 4096
 #define SS_LOCAL_EDGES_PER_CTA 8192
