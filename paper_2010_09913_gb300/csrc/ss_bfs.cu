@@ -53,6 +53,11 @@ namespace ss {
 #endif
 
 constexpr int PULL_THREADS = SS_PULL_THREADS;  // one block per SM
+#ifndef SS_PULL_SHORT_COLS
+#define SS_PULL_SHORT_COLS 4
+#endif
+constexpr int SHORT_COLS = SS_PULL_SHORT_COLS;  // chunks this short go several per warp
+
 // int4 col loads in flight per lane (4 slots each)
 template <int SR>
 __host__ __device__ constexpr int pull_step() { return SR == SS_REAL ? SS_PULL_STEP_REAL : SS_PULL_STEP; }
@@ -143,13 +148,19 @@ struct RowAcc {
 // Post-process one chunk (the frontier update of Section III-A): new rows are
 // the unvisited rows whose x_k is non-zero; they get level k, a parent and a
 // frontier bit; the chunk's SlimWork state is refreshed.  All lanes call.
-template <int SR, int C>
+//
+// GROUPED: the warp holds 32 / Q chunks at once, lanes g*Q .. g*Q+Q-1 owning all
+// rows of chunk g (own = this lane's group has a chunk); otherwise lanes 0..Q-1
+// own the rows of the warp's one chunk.
+template <int SR, int C, bool GROUPED = false>
 __device__ __forceinline__ void post_chunk(const Dev& d, int k, int chunk, int lane, int4 lv,
-                                           const RowAcc& a, Counters& cnt) {
+                                           const RowAcc& a, Counters& cnt, bool own = true) {
   constexpr int Q = C / 4;
-  const int R0 = chunk * C + 4 * lane;
+  const int lq = GROUPED ? lane % Q : lane;
+  const bool owner = GROUPED ? own : lane < Q;
+  const int R0 = chunk * C + 4 * lq;
   unsigned nib = 0, left = 0;
-  if (lane < Q) {
+  if (owner) {
     int L[4] = {lv.x, lv.y, lv.z, lv.w};
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
@@ -182,10 +193,22 @@ __device__ __forceinline__ void post_chunk(const Dev& d, int k, int chunk, int l
       cnt.nw += __popc(nib);
     }
   }
-  unsigned lo, hi;
-  gather_bits<C>(nib, lane, &lo, &hi);
-  const unsigned any_left = __any_sync(SS_FULL_MASK, left);
-  if (lane == 0) {
+  unsigned lo, hi, any_left;
+  if (GROUPED) {  // OR within each group of Q lanes
+    lo = (C <= 32 || lq < 8) ? nib << (4 * (lq & 7)) : 0u;
+    hi = (C > 32 && lq >= 8) ? nib << (4 * (lq - 8)) : 0u;
+    any_left = left;
+#pragma unroll
+    for (int o = 1; o < Q; o <<= 1) {
+      lo |= __shfl_xor_sync(SS_FULL_MASK, lo, o);
+      if (C > 32) hi |= __shfl_xor_sync(SS_FULL_MASK, hi, o);
+      any_left |= __shfl_xor_sync(SS_FULL_MASK, any_left, o);
+    }
+  } else {
+    gather_bits<C>(nib, lane, &lo, &hi);
+    any_left = __any_sync(SS_FULL_MASK, left);
+  }
+  if (owner && lq == 0) {
     store_bits<C>(d.fb[k & 1], chunk, lo, hi);
     d.act[chunk] = any_left ? 1 : 3;
   }
@@ -276,6 +299,55 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_pull(Dev d, int variant,
         carry_chunk<C>(d, k, __shfl_sync(SS_FULL_MASK, my_item.x, src), lane,
                        __shfl_sync(SS_FULL_MASK, a, src));
       }
+    }
+    // short whole chunks (at most SHORT_COLS columns, about half of all chunks of a
+    // skewed graph) go 32 / Q at a time, one group of Q lanes each
+    unsigned shortm = __ballot_sync(SS_FULL_MASK, a == 1 && my_item.w < 0 &&
+                                                      my_item.z - my_item.y <= SHORT_COLS);
+    todo &= ~shortm;
+    while (shortm) {
+      constexpr int GROUPS = 32 / Q;
+      int mysrc = -1;
+#pragma unroll
+      for (int g = 0; g < GROUPS; ++g) {
+        const int sidx = shortm ? __ffs(shortm) - 1 : -1;
+        if (lane / Q == g) mysrc = sidx;
+        shortm &= shortm - 1;
+      }
+      const bool own = mysrc >= 0;
+      const int sl = own ? mysrc : 0;
+      const int4 item = make_int4(__shfl_sync(SS_FULL_MASK, my_item.x, sl),
+                                  __shfl_sync(SS_FULL_MASK, my_item.y, sl),
+                                  __shfl_sync(SS_FULL_MASK, my_item.z, sl), -1);
+      const long long start = __shfl_sync(SS_FULL_MASK, my_start, sl);
+      const int lq = lane % Q;
+      const int ncols = own ? item.z - item.y : 0;
+      const int chunk = item.x;
+      const int4 lv = own ? *reinterpret_cast<const int4*>(d.lvl + chunk * C + 4 * lq)
+                          : make_int4(SS_PAD_LEVEL, SS_PAD_LEVEL, SS_PAD_LEVEL, SS_PAD_LEVEL);
+      const int L[4] = {lv.x, lv.y, lv.z, lv.w};
+      int first[4] = {-1, -1, -1, -1};
+      float sum[4] = {0.f, 0.f, 0.f, 0.f};
+      const int4* base = reinterpret_cast<const int4*>(d.col + start) + lq;
+      int4 c[SHORT_COLS];
+#pragma unroll
+      for (int u = 0; u < SHORT_COLS; ++u)
+        c[u] = (u < ncols) ? ld_stream(base + u * Q) : make_int4(-1, -1, -1, -1);
+#pragma unroll
+      for (int u = 0; u < SHORT_COLS; ++u)
+        if (u < ncols) scan_quad<SR>(d, sm, sbits, gbm, c[u], first, sum);
+      if (own && lq == 0) {
+        cnt.act += 1;
+        if (MODE != MODE_FILTERED) cnt.slots += (unsigned long long)ncols * C;
+      }
+      if (MODE == MODE_FILTERED) lane_slots += 4ull * ncols;
+      RowAcc acc;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        acc.best[r] = (first[r] >= 0 && L[r] == SS_INF) ? __ldg(d.perm + first[r]) : -1;
+        acc.sum[r] = sum[r];
+      }
+      post_chunk<SR, C, true>(d, k, chunk, lane, lv, acc, cnt, own);
     }
     while (todo) {
       const int src = __ffs(todo) - 1;
