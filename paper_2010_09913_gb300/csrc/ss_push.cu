@@ -184,30 +184,39 @@ constexpr int LOCAL_THREADS = 1024;
 constexpr int LOCAL_BATCH = 16;     // candidate edges per thread in flight
 constexpr int LOCAL_NEWCAP = 8192;  // new vertices per CTA kept in shared memory
 constexpr int LOCAL_POST = 2;       // new vertices per thread in flight in the post step
-constexpr int LOCAL_PER_THREAD = SS_LOCAL_SLICE / LOCAL_THREADS;
+constexpr int LOCAL_UNIT = 1024;    // edges of one slice entry; longer rows become several units
+constexpr int LOCAL_HUBCAP = 256;   // extra slice entries per CTA for the units of long rows
+constexpr int LOCAL_SLOTS = SS_LOCAL_SLICE + LOCAL_HUBCAP;
+constexpr int LOCAL_PER_THREAD = (LOCAL_SLOTS + LOCAL_THREADS - 1) / LOCAL_THREADS;
 constexpr int CTL_WORDS = (int)(sizeof(Ctl) / sizeof(unsigned));
 static_assert(sizeof(Ctl) % sizeof(unsigned) == 0, "control block copied as words");
 static_assert(SS_LOCAL_SLICE % LOCAL_THREADS == 0, "whole frontier entries per thread");
+static_assert(SS_LOCAL_CLUSTER_MAX * SS_LOCAL_EDGES_PER_CTA / LOCAL_UNIT <= LOCAL_HUBCAP,
+              "the units of the largest frontier fit one CTA");
 
 struct LocalPub {             // what each CTA tells every CTA of the cluster about a level
   int nsm;                    // new vertices it holds in shared memory
   int novf;                   // new vertices it put in the overflow list
   unsigned md;                // largest degree of the vertices it posted
+  int drop;                   // a unit of a long row found no room (the next level goes back)
   unsigned long long nd;      // their degree sum
 };
 
+// A CTA's slice of the frontier: entries 0 .. ns-1 are its equal share of the
+// vertex list (each with at most LOCAL_UNIT of its edges), then `hubn` units
+// carrying further LOCAL_UNIT-edge pieces of long rows, appended by any CTA.
 struct LocalSmem {
   Ctl ctl;                             // this CTA's copy of the control block
-  long long base[SS_LOCAL_SLICE];      // frontier slice: cs[u / C] + u % C
-  int pref[SS_LOCAL_SLICE];            // degrees, then their exclusive prefix
-  int orig[SS_LOCAL_SLICE];            // original ids (parent candidates)
-  int sid[2][SS_LOCAL_SLICE];          // vertex ids of the slice, by level parity
+  long long base[LOCAL_SLOTS];         // start of the entry's first edge in col
+  int pref[LOCAL_SLOTS];               // edge counts, then their exclusive prefix
+  int orig[LOCAL_SLOTS];               // original ids (parent candidates)
+  int sid[2][LOCAL_SLOTS];             // vertex ids, by level parity
   int nid[LOCAL_NEWCAP];               // vertices this CTA discovered
   long long wsum[LOCAL_THREADS / 32];
   unsigned long long red[LOCAL_THREADS / 32];
   unsigned redmax[LOCAL_THREADS / 32];
   LocalPub all[2][SS_LOCAL_CLUSTER_MAX];  // written by every CTA of the cluster, by level parity
-  int nnew, novf, es;
+  int nnew, novf, es, hubn, drop;
 };
 static_assert(sizeof(LocalSmem) <= 227 * 1024, "cluster push shared memory");
 
@@ -262,6 +271,33 @@ __device__ __forceinline__ void local_exit(LocalSmem& S, Ctl* c, const IterLaunc
   if (threadIdx.x == 0 && il.use_cond) cudaGraphSetConditional(il.cond, cond);
 }
 
+// Entry `slot` of CTA `owner`'s slice (parity p) gets vertex x's first edges; the
+// rest of a row longer than LOCAL_UNIT goes in LOCAL_UNIT-edge units to the
+// following CTAs in turn, appended after their shares (ns_of(o) entries).
+template <int C, typename NsOf>
+__device__ __forceinline__ void place_entry(LocalSmem& S, cg::cluster_group& cl, int G, int owner, int slot,
+                                            int p, int x, long long bx, int dv, int og, NsOf ns_of) {
+  LocalSmem* R = cl.map_shared_rank(&S, owner);
+  R->sid[p][slot] = x;
+  R->pref[slot] = min(dv, LOCAL_UNIT);
+  R->base[slot] = bx;
+  R->orig[slot] = og;
+  int o = owner;
+  for (int j0 = LOCAL_UNIT; j0 < dv; j0 += LOCAL_UNIT) {
+    o = (o + 1 == G) ? 0 : o + 1;
+    LocalSmem* T = cl.map_shared_rank(&S, o);
+    const int at = ns_of(o) + atomicAdd(&T->hubn, 1);
+    if (at >= LOCAL_SLOTS) {  // no room: the cluster hands this level back instead
+      S.drop = 1;
+      continue;
+    }
+    T->sid[p][at] = x;
+    T->pref[at] = min(dv - j0, LOCAL_UNIT);
+    T->base[at] = bx + (long long)j0 * C;
+    T->orig[at] = og;
+  }
+}
+
 extern __shared__ __align__(16) unsigned char ss_local_smem[];
 
 // CTA r's first entry of a list of `total` entries split into G = 2^lg equal
@@ -294,6 +330,10 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) k_push_local(Dev d, IterLaun
     unsigned* dst = reinterpret_cast<unsigned*>(&S.ctl);
     for (int i = tid; i < CTL_WORDS; i += LOCAL_THREADS) dst[i] = src[i];
     if (rank == 0 && tid < 2) d.qovf_n[tid] = 0ull;
+    if (tid == 0) {
+      S.hubn = 0;
+      S.drop = 0;
+    }
   }
   cl.sync();  // every CTA holds its copy before CTA 0 can write the block back
   if (S.ctl.done) return;  // the same in every CTA; no shared memory was shared yet
@@ -318,25 +358,28 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) k_push_local(Dev d, IterLaun
     const int p1 = (k - 1) & 1;
     const long long lo = share(nf, rank, lg);
     const int ns = (int)(share(nf, rank + 1, lg) - lo);
+    auto ns_of = [&](int o) { return (int)(share(nf, o + 1, lg) - share(nf, o, lg)); };
     for (int i = tid; i < ns; i += LOCAL_THREADS) {
       const int u = __ldcg(d.qlist[p1] + lo + i);
-      S.sid[p1][i] = u;
+      int dv, og;
+      long long bx;
       if (have_list) {
-        S.pref[i] = __ldcg(d.qdeg[p1] + lo + i);
-        S.base[i] = __ldcg(d.qbase[p1] + lo + i);
-        S.orig[i] = __ldcg(d.qorig[p1] + lo + i);
+        dv = __ldcg(d.qdeg[p1] + lo + i);
+        bx = __ldcg(d.qbase[p1] + lo + i);
+        og = __ldcg(d.qorig[p1] + lo + i);
       } else {
-        S.pref[i] = __ldg(d.rdeg + u);
-        S.base[i] = __ldg(d.cs + u / C) + (u % C);
-        S.orig[i] = __ldg(d.perm + u);
+        dv = __ldg(d.rdeg + u);
+        bx = __ldg(d.cs + u / C) + (u % C);
+        og = __ldg(d.perm + u);
       }
+      place_entry<C>(S, cl, G, rank, i, p1, u, bx, dv, og, ns_of);
     }
     const long long n2 = (have_list && S.ctl.list_prev_ok) ? (long long)S.ctl.qlen[k & 1] : 0;
     const long long lo2 = share(n2, rank, lg), hi2 = share(n2, rank + 1, lg);
     unsigned* fbk = d.fb[k & 1];
     for (long long i = lo2 + tid; i < hi2; i += LOCAL_THREADS) fbk[__ldcg(d.qlist[k & 1] + i) >> 5] = 0u;
   }
-  __syncthreads();  // the first slice is in place
+  cl.sync();  // the first slices, with the units of long rows, are in place
   int ns_prev = 0;  // entries of S.sid[k&1]: this CTA's slice of level k-2 (after the first level)
   unsigned long long reached = S.ctl.reached;  // every thread tracks the stop condition
   for (int lev = 0;; ++lev) {
@@ -350,7 +393,8 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) k_push_local(Dev d, IterLaun
     }
     const int p1 = (k - 1) & 1, p0 = k & 1;
     unsigned* fbk = d.fb[p0];
-    const int ns = (int)(share(nf, rank + 1, lg) - share(nf, rank, lg));
+    const int nsv = (int)(share(nf, rank + 1, lg) - share(nf, rank, lg));  // vertices
+    const int ns = nsv + S.hubn;  // slice entries: vertices, then units of long rows
     for (int i = tid; i < ns_prev; i += LOCAL_THREADS) fbk[S.sid[p0][i] >> 5] = 0u;  // level k-2
     if (tid == 0) {
       S.nnew = 0;
@@ -482,6 +526,10 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) k_push_local(Dev d, IterLaun
       dst->novf = S.novf;
     }
     if (rank == 0 && tid == 0) d.qovf_n[p1] = 0ull;  // the next level's overflow counter
+    if (tid == 0) {  // units for the next level are appended after this barrier
+      S.hubn = 0;
+      S.drop = 0;
+    }
     cl.sync();  // #1: every scatter is done, so parents and sums are final
     // ---- list positions (every warp alike): this CTA's list, then its share of the overflow ----
     long long tot, novf, off;
@@ -502,7 +550,9 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) k_push_local(Dev d, IterLaun
     const int nsm = S.all[p0][rank].nsm;
     const long long olo = share(novf, rank, lg);
     const int cnt = nsm + (int)(share(novf, rank + 1, lg) - olo);
-    const bool next_here = local_fits(d, (unsigned long long)tot, 0ull);  // next slices fit
+    // the next slices are filled only for a frontier the cluster will likely take:
+    // past local_max_e / 4 vertices its edges almost surely outgrow the cluster
+    const bool next_here = local_fits(d, (unsigned long long)tot, 0ull) && tot <= d.local_max_e / 4;
     // ---- post: level, parent, value, frontier bit and list record of each new vertex;
     // its data also goes straight to the CTA that takes it in the next level ----
     unsigned long long nd = 0;
@@ -547,12 +597,8 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) k_push_local(Dev d, IterLaun
         d.qorig[p0][at] = og[q];
         if (next_here) {
           const int r = share_owner(at, tot, lg);
-          const int slot = (int)(at - share(tot, r, lg));
-          LocalSmem* R = cl.map_shared_rank(&S, r);
-          R->sid[p0][slot] = x;
-          R->pref[slot] = dv[q];
-          R->base[slot] = bx;
-          R->orig[slot] = og[q];
+          place_entry<C>(S, cl, G, r, (int)(at - share(tot, r, lg)), p0, x, bx, dv[q], og[q],
+                         [&](int o) { return (int)(share(tot, o + 1, lg) - share(tot, o, lg)); });
         }
         nd += (unsigned long long)dv[q];
         md = max(md, (unsigned)dv[q]);
@@ -577,12 +623,14 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) k_push_local(Dev d, IterLaun
         LocalPub* dst = &cl.map_shared_rank(&S, lane)->all[p0][rank];
         dst->nd = w;
         dst->md = m;
+        dst->drop = S.drop;
       }
     }
     cl.sync();  // #2: every record, slice and statistic of level k is in place
     // ---- totals (every warp alike) and the stop decision ----
     unsigned long long td = lane < G ? S.all[p0][lane].nd : 0ull;
     unsigned tm = lane < G ? S.all[p0][lane].md : 0u;
+    const bool dropped = __any_sync(SS_FULL_MASK, lane < G && S.all[p0][lane].drop != 0);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) td += __shfl_xor_sync(SS_FULL_MASK, td, o);
     tm = __reduce_max_sync(SS_FULL_MASK, tm);
@@ -600,7 +648,7 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) k_push_local(Dev d, IterLaun
       local_exit(S, c, il, 0u, cl);
       return;
     }
-    if (!next_here) {  // the next frontier does not fit: hand back before using it
+    if (!next_here || dropped) {  // the next frontier does not fit: hand back before using it
       ++k;
       if (tid == 0) {
         S.ctl.list_level = k - 1;
@@ -609,7 +657,7 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) k_push_local(Dev d, IterLaun
       local_exit(S, c, il, 1u, cl);
       return;
     }
-    ns_prev = ns;  // this level's frontier is level (k+1)-2
+    ns_prev = nsv;  // this level's frontier is level (k+1)-2
     nf = tot;
     E = (long long)td;
     ++k;

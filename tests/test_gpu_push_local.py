@@ -63,6 +63,17 @@ def wide_star(tail=200, leaves=140000, seed=3):
     return relabelled(hub + 1 + leaves, e, seed, f"widestar{leaves}")
 
 
+def hub_graph(tail=50, leaves=100000, seed=5):
+    """A path into a hub with 100000 leaves, every leaf also tied to a second hub:
+    the hubs' rows are longer than one cluster-push slice entry, so their edges
+    are spread over the cluster in units."""
+    e = [(i, i + 1) for i in range(tail)]
+    hub1, hub2 = tail, tail + 1 + leaves
+    for j in range(leaves):
+        e += [(hub1, tail + 1 + j), (tail + 1 + j, hub2)]
+    return relabelled(hub2 + 1, e, seed, f"hubs{leaves}")
+
+
 def expected(g, r):
     d = oracle.bfs_queue(g.row_ptr, g.col, int(r))
     return d, oracle.dp(g.row_ptr, g.col, d, int(r))
@@ -123,6 +134,18 @@ def test_edge_budget_hand_back(loop):
         for policy in ["push", "heuristic"]:
             seq = check(G, g, r, sr, policy)
             assert seq[0] == LOCAL and seq[-1] != LOCAL, seq  # the hub's 140001 edges
+    G.close()
+
+
+@pytest.mark.parametrize("loop", [1, 0])
+def test_long_rows_split_into_units(loop):
+    g, p = hub_graph()
+    G = ss.SlimSellGraph.from_host(g.row_ptr, g.col, C=32, sigma=g.n, split_w=256)
+    G.set_option(ss.OPT_DEVICE_LOOP, loop)
+    for r in [int(p[0]), int(p[50]), int(p[40000]), int(p[100051])]:  # path end, hubs, a leaf
+        for sr in SEMIRINGS:
+            seq = check(G, g, r, sr, "push")
+            assert seq.count(LOCAL) >= 1, seq
     G.close()
 
 
