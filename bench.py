@@ -241,6 +241,31 @@ def time_policy(ss, torch, h, roots, policy, stream, runs_edges):
     return runs_edges / (ms / 1000.0) / 1e9, ms
 
 
+SELECTOR_MARGIN = 100  # thousandths of a log-time unit the network must gain over the rule
+
+
+def train_selector(ss, torch, g, h, args):
+    """Collect per-iteration variant timings and fit the selector on the GPU."""
+    from paper_2010_09913_gb300 import selector
+    t0 = time.perf_counter()
+    Xs, Ts, Ms = [], [], []
+    G = ss.SlimSellGraph.wrap(h, g.n)
+    X, T, M = selector.collect(G, gg.roots(g, 64, seed=99), "tropical", repeats=2, max_per_root=24)
+    Xs.append(X); Ts.append(T); Ms.append(M)
+    for tg, nr in ((gg.kronecker(14, seed=7), 8), (gg.kronecker(18, seed=7), 16),
+                   (gg.lattice(512, 0.05, seed=7), 4), (gg.erdos_renyi(1 << 20, 16.0, seed=7), 8)):
+        G = ss.SlimSellGraph.from_host(tg.row_ptr, tg.col, C=32, sigma=tg.n, split_w=args.split_w)
+        X, T, M = selector.collect(G, gg.roots(tg, nr, seed=8), "tropical", repeats=2, max_per_root=24)
+        Xs.append(X); Ts.append(T); Ms.append(M)
+        G.close()
+    w, loss = selector.train(np.concatenate(Xs), np.concatenate(Ts), np.concatenate(Ms), steps=12000,
+                             lr=1e-3)
+    return w, {"samples": int(sum(x.shape[0] for x in Xs)), "final_loss": loss,
+               "seconds": time.perf_counter() - t0, "margin_log_units": SELECTOR_MARGIN / 1000.0,
+               "graphs": f"kronecker {args.scale} (64 roots other than the timed ones), kronecker 14 "
+                         "and 18, lattice 512^2 (5% deleted), ER 2^20 (mean deg 16)"}
+
+
 def batched_learned(ss, torch, g, h, roots, args, stream, dev, runs_edges):
     """On the same graph: heuristic and learned per-iteration schedules of
     single-source BFS, and bit-packed multi-source batches."""
@@ -250,19 +275,14 @@ def batched_learned(ss, torch, g, h, roots, args, stream, dev, runs_edges):
     out["plain_slimwork_single"] = gte
     gte, _ = time_policy(ss, torch, h, roots, ss.V_HEURISTIC, stream, runs_edges)
     out["heuristic_single"] = gte
-    # train the selector on other (smaller) generated graphs, evaluate on this one
-    t0 = time.perf_counter()
-    Xs, Ts, Ms = [], [], []
-    for tg in (gg.kronecker(16, seed=7), gg.lattice(256, 0.05, seed=7), gg.erdos_renyi(1 << 16, 16.0, seed=7)):
-        G = ss.SlimSellGraph.from_host(tg.row_ptr, tg.col, C=32, sigma=tg.n, split_w=args.split_w)
-        X, T, M = selector.collect(G, gg.roots(tg, 3, seed=8), "tropical", repeats=2)
-        Xs.append(X); Ts.append(T); Ms.append(M)
-        G.close()
-    w, loss = selector.train(np.concatenate(Xs), np.concatenate(Ts), np.concatenate(Ms), steps=3000)
-    out["selector_training"] = {"samples": int(sum(x.shape[0] for x in Xs)), "final_loss": loss,
-                                "seconds": time.perf_counter() - t0,
-                                "graphs": "kronecker 16, lattice 256^2 (5% deleted), ER 2^16 (mean deg 16)"}
+    # train the selector on timings the method generates on the configurations'
+    # graph families: Kronecker scale 14 and 18, this scale-22 graph with other
+    # roots than the timed ones, a lattice and an Erdos-Renyi graph (24 evenly
+    # spaced iterations per run at most, so long runs do not dominate)
+    w, tr = train_selector(ss, torch, g, h, args)
+    out["selector_training"] = tr
     ss.slimsell_selector_load(h, w)
+    ss.slimsell_set_option(h, ss.OPT_SELECTOR_MARGIN, SELECTOR_MARGIN)
     for sr in SEMIRINGS:  # build the learned loop graphs outside the timed region
         ss.slimsell_bfs(h, int(roots[0]), SR_ID[sr], ss.V_LEARNED, None, None, stream)
     gte, _ = time_policy(ss, torch, h, roots, ss.V_LEARNED, stream, runs_edges)
@@ -291,6 +311,7 @@ def batched_learned(ss, torch, g, h, roots, args, stream, dev, runs_edges):
         out[f"multi_{k}_ms"] = ms
         del dist
     ss.slimsell_selector_load(h, None)
+    out["selector_weights"] = w
     best_single = max(out["heuristic_single"], out["learned_single"])
     out["best_batched_or_learned_over_plain"] = max(best_single, out["multi_1024"]) / out["plain_slimwork_single"]
     return out
@@ -401,7 +422,42 @@ def roofline_at_scale(ss, torch, scale, nroots, split_w, stream, dev):
     return out
 
 
-def high_diameter(ss, torch, stream, dev, nroots=16):
+def selector_heldout(ss, torch, stream, dev, weights):
+    """The selector trained above, on graphs it never saw: Kronecker scale 25
+    (edgefactor 16) and a 8192 x 8192 lattice with 5% of its edges deleted;
+    tropical; learned against the frontier-size rule and plain SlimWork."""
+    out = {}
+    for name, g, nr, nplain in (("kronecker scale 25", gg.kronecker(25, seed=3), 64, 64),
+                                ("lattice 8192^2 (5% deleted)", gg.lattice(8192, 0.05, seed=3), 8, 1)):
+        roots = gg.roots(g, nr, seed=4)
+        rp_d = torch.from_numpy(g.row_ptr).to(dev)
+        col_d = torch.from_numpy(g.col).to(dev)
+        h = ss.slimsell_build(rp_d, col_d, g.n, g.nnz, 32, g.n, 256, stream)
+        del rp_d, col_d, g
+        ss.slimsell_selector_load(h, weights)
+        ss.slimsell_set_option(h, ss.OPT_SELECTOR_MARGIN, SELECTOR_MARGIN)
+        res = {"roots": nr}
+        for pol_name, pol, rs in (("learned", ss.V_LEARNED, roots), ("heuristic", ss.V_HEURISTIC, roots),
+                                  ("slimwork", ss.V_SLIMWORK, roots[:nplain])):
+            ss.slimsell_bfs(h, int(rs[0]), SR_ID["tropical"], pol, None, None, stream)  # warm-up
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            ms, edges = 0.0, 0
+            for r in rs:
+                torch.cuda.synchronize()
+                e0.record(stream)
+                ss.slimsell_bfs(h, int(r), SR_ID["tropical"], pol, None, None, stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms += e0.elapsed_time(e1)
+                edges += ss.slimsell_get_run_stats(h)[0].reached_degree // 2
+            res[pol_name] = {"gteps": edges / (ms / 1000.0) / 1e9, "ms_per_run": ms / len(rs), "runs": len(rs)}
+        ss.slimsell_destroy(h)
+        out[name] = res
+    return out
+
+
+def high_diameter(ss, torch, stream, dev, weights=None, nroots=16):
     """High-diameter and low-skew graphs: a 4096 x 4096 lattice with 5% of its
     edges deleted and an Erdos-Renyi graph (n = 2^22, mean degree 16); sel-max
     and tropical; C = 32, sigma = N; 16 seeded roots.  The adaptive schedule
@@ -418,9 +474,13 @@ def high_diameter(ss, torch, stream, dev, nroots=16):
         del rp_d, col_d
         res = {"n": g.n, "nnz": g.nnz, "roots": nroots}
         lattice = name.startswith("lattice")
+        pols = [("heuristic", ss.V_HEURISTIC, roots), ("slimwork", ss.V_SLIMWORK, roots[:2] if lattice else roots)]
+        if weights is not None:
+            ss.slimsell_selector_load(h, weights)
+            ss.slimsell_set_option(h, ss.OPT_SELECTOR_MARGIN, SELECTOR_MARGIN)
+            pols.append(("learned", ss.V_LEARNED, roots))
         for sr in ("selmax", "tropical"):
-            for pol_name, pol, rs in (("heuristic", ss.V_HEURISTIC, roots),
-                                      ("slimwork", ss.V_SLIMWORK, roots[:2] if lattice else roots)):
+            for pol_name, pol, rs in pols:
                 ss.slimsell_bfs(h, int(rs[0]), SR_ID[sr], pol, None, None, stream)  # warm-up
                 edges, iters, local = 0, 0, 0
                 e0 = torch.cuda.Event(enable_timing=True)
@@ -462,6 +522,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-scale24", action="store_true")
     ap.add_argument("--no-high-diameter", action="store_true")
+    ap.add_argument("--selector-heldout", action="store_true",
+                    help="also evaluate the selector on held-out Kronecker 25 and lattice 8192^2")
     ap.add_argument("--batch-graphs", type=int, default=200)
     args = ap.parse_args()
     world, rank, local, pg = dist_setup()
@@ -586,9 +648,11 @@ def main():
             "layout": {"slots": info.slots, "padding": info.padding, "n_items": info.n_items,
                        "n_split_chunks": info.n_split_chunks, "max_degree": info.max_degree}}
 
+    sel_w = None
     if not args.no_batched and rank == 0:
         line["batched_learned"] = batched_learned(ss, torch, g, h, roots, args, stream, dev,
                                                   edges_per_step)
+        sel_w = line["batched_learned"].pop("selector_weights")
         line["batched_graphs"] = batched_graphs(ss, torch, args.batch_graphs, stream, dev)
     if not args.no_e2e:
         line["e2e"] = e2e_measure(ss, torch, g, roots, args, stream, dev, pg)
@@ -601,7 +665,10 @@ def main():
         line["scale24"] = roofline_at_scale(ss, torch, 24, 8, args.split_w, stream, dev)
     if not args.no_high_diameter and rank == 0:
         torch.cuda.empty_cache()
-        line["high_diameter"] = high_diameter(ss, torch, stream, dev)
+        line["high_diameter"] = high_diameter(ss, torch, stream, dev, sel_w)
+    if args.selector_heldout and rank == 0 and sel_w is not None:
+        torch.cuda.empty_cache()
+        line["selector_heldout"] = selector_heldout(ss, torch, stream, dev, sel_w)
     if rank == 0 and world == 1 and not args.no_cpu:
         edges, t_cpu, nruns = cpu_oracle_sample(g, roots, 20.0)
         line["cpu_baseline"] = {"value": edges / t_cpu / 1e9, "unit": "GTEPS", "cores": 1,

@@ -208,8 +208,11 @@ typedef enum {
                              computed on the fly inside the iterations                        */
   SS_OPT_SMEM_BYTES = 2,  /* bytes of the frontier bitmap staged in shared memory per block,
                              0 .. 212992 (default 212992); results do not depend on it          */
-  SS_OPT_DEVICE_LOOP = 3  /* 1 (default): iterate on the device in a conditional CUDA graph;
+  SS_OPT_DEVICE_LOOP = 3, /* 1 (default): iterate on the device in a conditional CUDA graph;
                              0: the host launches each iteration and reads its counter          */
+  SS_OPT_SELECTOR_MARGIN = 4 /* learned policy, in thousandths of a log-time unit, 0 .. 100000
+                             (default 0): the network's choice replaces the frontier-size rule's
+                             only when it predicts a gain larger than this margin             */
 } ss_option;
 
 /* Set a handle option (applies to later calls).  Errors: SS_ERR_INVALID. */

@@ -745,6 +745,15 @@ ss_status add_loop_node(slimsell_graph* h, const Dev& d, int sr, int policy, cud
   return s;
 }
 
+void drop_loop_graphs(slimsell_graph* h) {
+  for (auto& row : h->loop_exec)
+    for (auto& e : row)
+      if (e) {
+        cudaGraphExecDestroy(e);
+        e = nullptr;
+      }
+}
+
 // The single-call loop graph, built once per (semiring, policy, staged-prefix
 // size) and cached in the handle.
 static ss_status loop_graph(slimsell_graph* h, const Dev& d, int sr, int policy,
@@ -953,6 +962,14 @@ ss_status slimsell_set_option(slimsell_handle h, int32_t option, int64_t value) 
       return SS_OK;
     case SS_OPT_DEVICE_LOOP:
       h->device_loop = value ? 1 : 0;
+      return SS_OK;
+    case SS_OPT_SELECTOR_MARGIN:
+      if (value < 0 || value > 100000) {
+        ss::set_error("slimsell_set_option: selector margin must be in [0, 100000] thousandths");
+        return SS_ERR_INVALID;
+      }
+      h->sel_margin = (float)value / 1000.0f;
+      ss::drop_loop_graphs(h);
       return SS_OK;
     case SS_OPT_SMEM_BYTES:
       if (value < 0 || value > SS_SMEM_MAX_BYTES) {

@@ -618,6 +618,7 @@ ss::Dev slimsell_graph::dev() const {
   d.fr = fr; d.par = par; d.xacc = xacc; d.xpar = xpar; d.arrive = arrive;
   d.units = units; d.units_cap = units_cap;
   d.pbest = pbest; d.psum = psum; d.touched = touched; d.mlp = mlp; d.feats = feats;
+  d.sel_margin = sel_margin;
   for (int b = 0; b < 2; ++b) {
     d.qlist[b] = qlist[b]; d.qdeg[b] = qdeg[b]; d.qbase[b] = qbase[b]; d.qorig[b] = qorig[b];
   }

@@ -105,6 +105,7 @@ struct Dev {
   int local_cluster;    // CTAs in the cluster push's cluster
   long long local_max_nf, local_max_e;  // largest frontier (vertices, edges) it takes
   const float* mlp;     // selector weights (16-64-64-4 MLP), or NULL
+  float sel_margin;     // learned policy: predicted log-time gain needed to leave the heuristic
   float* feats;         // [iter_cap][16] selector features of each iteration of the last run
   long long nnz, total_slots;
   unsigned long long reach_cap;  // most reached units a correct run can count (n, or n * k)
@@ -153,6 +154,7 @@ struct slimsell_graph {
   unsigned long long* qovf_n = nullptr;
   int local_cluster = 0;
   float* mlp = nullptr;       // selector weights on the device (NULL until loaded)
+  float sel_margin = 0.0f;    // see SS_OPT_SELECTOR_MARGIN
   float* feats = nullptr;
   // multi-source scratch ([n_pad][W] words), grown on demand
   int multi_w = 0;

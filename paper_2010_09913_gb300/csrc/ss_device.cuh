@@ -191,7 +191,8 @@ ss_status launch_push(const slimsell_graph* h, const Dev& d, int sr, const IterL
                       cudaStream_t st);
 ss_status launch_push_local(const slimsell_graph* h, const Dev& d, int sr, const IterLaunch& il,
                             int max_levels, cudaStream_t st);
-int push_local_cluster_size();  // CTAs per cluster of the cluster push on the current device (0: none)
+int push_local_cluster_size();
+void drop_loop_graphs(slimsell_graph* h);  // forget captured loops (they hold handle state)  // CTAs per cluster of the cluster push on the current device (0: none)
 ss_status launch_decide(const slimsell_graph* h, const Dev& d, int policy,
                         cudaGraphConditionalHandle sw, int use_sw, cudaStream_t st);
 ss_status add_decide_node(const slimsell_graph* h, const Dev& d, int policy,

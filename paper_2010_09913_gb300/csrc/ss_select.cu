@@ -137,6 +137,11 @@ __global__ void k_decide(Dev d, int policy, cudaGraphConditionalHandle sw, int u
         if (v == VAR_PUSH && !push_fits(d, c)) continue;
         if (y[v] < y[best]) best = v;
       }
+      // fallback: keep the frontier-size rule's choice unless the network
+      // predicts a gain larger than the margin (in log-time units)
+      int hv = choice;
+      if (hv == VAR_PUSH && !push_fits(d, c)) hv = VAR_FILTERED;
+      if (d.sel_margin > 0.0f && y[best] + d.sel_margin >= y[hv]) best = hv;
       choice = best;
     }
     __syncthreads();
@@ -314,6 +319,7 @@ ss_status slimsell_selector_load(slimsell_handle h, const float* h_weights, int6
     return SS_ERR_INVALID;
   }
   if (!h_weights) {  // unload: the learned policy falls back to the heuristic
+    ss::drop_loop_graphs(h);  // captured loops hold the weight pointer
     if (h->mlp) cudaFree(h->mlp);
     h->mlp = nullptr;
     return SS_OK;
@@ -328,12 +334,7 @@ ss_status slimsell_selector_load(slimsell_handle h, const float* h_weights, int6
     if (s != SS_OK) return s;
   }
   SS_CUDA(cudaMemcpy(h->mlp, h_weights, sizeof(float) * SS_SELECTOR_PARAMS, cudaMemcpyHostToDevice));
-  for (auto& row : h->loop_exec)  // captured loops hold the old weight pointer
-    for (auto& e : row)
-      if (e) {
-        cudaGraphExecDestroy(e);
-        e = nullptr;
-      }
+  ss::drop_loop_graphs(h);  // captured loops hold the old weight pointer
   return SS_OK;
 }
 

@@ -42,8 +42,11 @@ def _profiled_run(G, root: int, semiring: str, policy: str):
     return ns, var, feats
 
 
-def collect(G, roots, semiring: str = "tropical", repeats: int = 3):
-    """Features X [N, 16], log-microsecond targets T [N, 4] and masks M [N, 4]."""
+def collect(G, roots, semiring: str = "tropical", repeats: int = 3, max_per_root: int = 0):
+    """Features X [N, 16], log-microsecond targets T [N, 4] and masks M [N, 4].
+
+    max_per_root > 0 keeps that many evenly spaced iterations of each run, so
+    that a high-diameter graph (thousands of levels) does not drown the others."""
     xs, ts, ms = [], [], []
     for r in roots:
         per_var, feats = [], None
@@ -61,9 +64,12 @@ def collect(G, roots, semiring: str = "tropical", repeats: int = 3):
         for vi, (ns, ok) in enumerate(per_var):
             T[:, vi] = np.log(ns / 1000.0 + 1.0)
             M[:, vi] = ok.astype(np.float32)
-        xs.append(feats.astype(np.float32))
-        ts.append(T)
-        ms.append(M)
+        keep = np.arange(iters)
+        if max_per_root > 0 and iters > max_per_root:
+            keep = np.unique(np.linspace(0, iters - 1, max_per_root).round().astype(np.int64))
+        xs.append(feats.astype(np.float32)[keep])
+        ts.append(T[keep])
+        ms.append(M[keep])
     return np.concatenate(xs), np.concatenate(ts), np.concatenate(ms)
 
 

@@ -179,3 +179,31 @@ def test_selector_training_pipeline():
     assert res["learned"] <= worst_fixed, res
     for G, _ in handles:
         G.close()
+
+
+def test_learned_margin_falls_back_to_the_rule():
+    """With a margin no prediction can clear, the learned policy runs exactly the
+    frontier-size rule's schedule; unloading the weights after a learned run
+    leaves a usable handle (the captured loop is rebuilt)."""
+    g = gg.kronecker(13, seed=5)
+    G = ss.SlimSellGraph.from_host(g.row_ptr, g.col, C=32, sigma=g.n, split_w=64)
+    r = int(gg.roots(g, 1, seed=3)[0])
+    d, p = expected(g, r)
+    G.bfs(r, "tropical", "heuristic")
+    want = variants_of(G, 64)
+    ss.slimsell_selector_load(G.h, gg.mlp_weights(11, scale=3.0))
+    G.set_option(ss.OPT_SELECTOR_MARGIN, 100000)
+    dist, parent = G.bfs(r, "tropical", "learned")
+    torch.cuda.synchronize()
+    assert variants_of(G, 64) == want
+    np.testing.assert_array_equal(dist.cpu().numpy(), d)
+    with pytest.raises(ss.SlimSellError):
+        G.set_option(ss.OPT_SELECTOR_MARGIN, -1)
+    G.set_option(ss.OPT_SELECTOR_MARGIN, 0)
+    ss.slimsell_selector_load(G.h, None)
+    dist, parent = G.bfs(r, "tropical", "learned")
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(parent.cpu().numpy(), p)
+    assert variants_of(G, 64) == want  # no weights: the rule
+    G.close()
+
