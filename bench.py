@@ -457,7 +457,7 @@ def selector_heldout(ss, torch, stream, dev, weights):
     return out
 
 
-def high_diameter(ss, torch, stream, dev, weights=None, nroots=16):
+def high_diameter(ss, torch, stream, dev, weights=None, nroots=16, host_loop=False):
     """High-diameter and low-skew graphs: a 4096 x 4096 lattice with 5% of its
     edges deleted and an Erdos-Renyi graph (n = 2^22, mean degree 16); sel-max
     and tropical; C = 32, sigma = N; 16 seeded roots.  The adaptive schedule
@@ -472,6 +472,8 @@ def high_diameter(ss, torch, stream, dev, weights=None, nroots=16):
         col_d = torch.from_numpy(g.col).to(dev)
         h = ss.slimsell_build(rp_d, col_d, g.n, g.nnz, 32, g.n, 256, stream)
         del rp_d, col_d
+        if host_loop:
+            ss.slimsell_set_option(h, ss.OPT_DEVICE_LOOP, 0)
         res = {"n": g.n, "nnz": g.nnz, "roots": nroots}
         lattice = name.startswith("lattice")
         pols = [("heuristic", ss.V_HEURISTIC, roots), ("slimwork", ss.V_SLIMWORK, roots[:2] if lattice else roots)]
@@ -522,6 +524,10 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-scale24", action="store_true")
     ap.add_argument("--no-high-diameter", action="store_true")
+    ap.add_argument("--only", choices=["high-diameter"], default=None,
+                    help="run one section alone and print it (profiling runs)")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="host-driven iteration loop (kernels visible to a profiler)")
     ap.add_argument("--selector-heldout", action="store_true",
                     help="also evaluate the selector on held-out Kronecker 25 and lattice 8192^2")
     ap.add_argument("--batch-graphs", type=int, default=200)
@@ -538,6 +544,11 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)
+    if args.only == "high-diameter":
+        if rank == 0:
+            print(json.dumps({"high_diameter": high_diameter(ss, torch, stream, dev, None, nroots=args.roots,
+                                                             host_loop=args.host_loop)}), flush=True)
+        return
 
     g = gg.kronecker(args.scale, seed=1)
     roots = gg.roots(g, args.roots, seed=2 + 1000 * rank)

@@ -668,16 +668,17 @@ static ss_status launch_iteration(const slimsell_graph* h, const Dev& d, int sr,
   }
 }
 
-// Queue the kernels of one iteration of the given variant.  The single-block
-// push runs as many small levels as it can in the device-side loop, and one
-// level per launch when the host drives the loop (per-level timing).
+// Queue the kernels of one iteration of the given variant.  The cluster push
+// runs as many small levels as it can per launch, except under per-level
+// timing (profiling on), where it runs one.
 static ss_status launch_variant(const slimsell_graph* h, const Dev& d, int sr, int variant,
                                 const IterLaunch& il, cudaStream_t st) {
   switch (variant) {
     case VAR_FULL: return launch_iteration(h, d, sr, MODE_FULL, il, st);
     case VAR_SLIMWORK: return launch_iteration(h, d, sr, MODE_SLIMWORK, il, st);
     case VAR_PUSH: return launch_push(h, d, sr, il, st);
-    case VAR_PUSH_LOCAL: return launch_push_local(h, d, sr, il, il.use_cond ? (1 << 30) : 1, st);
+    case VAR_PUSH_LOCAL:
+      return launch_push_local(h, d, sr, il, (il.use_cond || !h->profiling) ? (1 << 30) : 1, st);
     default: return launch_iteration(h, d, sr, MODE_FILTERED, il, st);
   }
 }
