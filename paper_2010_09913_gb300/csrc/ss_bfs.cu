@@ -228,9 +228,14 @@ __device__ __forceinline__ void carry_chunk(const Dev& d, int k, int chunk, int 
 
 // Scan the slots of one quad: record the first frontier hit per row and, for
 // the real semiring, add the values of all hits.
+// live: bit r set while row r is unvisited.  Visited rows keep their value, so
+// the real semiring gathers frontier values for live rows only.  (Skipping the
+// bit lookups of rows already hit, for the other semirings, measured slower:
+// the predicated lookups cost more issue slots than they save.)
 template <int SR>
 __device__ __forceinline__ void scan_quad(const Dev& d, const unsigned* sm, int sbits,
-                                          const unsigned* gbm, int4 c, int first[4], float sum[4]) {
+                                          const unsigned* gbm, int4 c, int first[4], float sum[4],
+                                          unsigned live) {
   const int cc[4] = {c.x, c.y, c.z, c.w};
   unsigned hit[4];
 #pragma unroll
@@ -238,7 +243,7 @@ __device__ __forceinline__ void scan_quad(const Dev& d, const unsigned* sm, int 
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
     first[r] = (hit[r] && first[r] < 0) ? cc[r] : first[r];
-    if (SR == SS_REAL && hit[r]) sum[r] += __ldg(d.fr + cc[r]);
+    if (SR == SS_REAL && hit[r] && (live >> r & 1u)) sum[r] += __ldg(d.fr + cc[r]);
   }
 }
 
@@ -326,6 +331,8 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_pull(Dev d, int variant,
       const int4 lv = own ? *reinterpret_cast<const int4*>(d.lvl + chunk * C + 4 * lq)
                           : make_int4(SS_PAD_LEVEL, SS_PAD_LEVEL, SS_PAD_LEVEL, SS_PAD_LEVEL);
       const int L[4] = {lv.x, lv.y, lv.z, lv.w};
+      const unsigned live = (L[0] == SS_INF ? 1u : 0u) | (L[1] == SS_INF ? 2u : 0u) |
+                            (L[2] == SS_INF ? 4u : 0u) | (L[3] == SS_INF ? 8u : 0u);
       int first[4] = {-1, -1, -1, -1};
       float sum[4] = {0.f, 0.f, 0.f, 0.f};
       const int4* base = reinterpret_cast<const int4*>(d.col + start) + lq;
@@ -335,7 +342,7 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_pull(Dev d, int variant,
         c[u] = (u < ncols) ? ld_stream(base + u * Q) : make_int4(-1, -1, -1, -1);
 #pragma unroll
       for (int u = 0; u < SHORT_COLS; ++u)
-        if (u < ncols) scan_quad<SR>(d, sm, sbits, gbm, c[u], first, sum);
+        if (u < ncols) scan_quad<SR>(d, sm, sbits, gbm, c[u], first, sum, live);
       if (own && lq == 0) {
         cnt.act += 1;
         if (MODE != MODE_FILTERED) cnt.slots += (unsigned long long)ncols * C;
@@ -371,6 +378,8 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_pull(Dev d, int variant,
       // levels of this lane's 4 rows (prefetched; only this chunk's post writes them)
       const int4 lv = *reinterpret_cast<const int4*>(d.lvl + chunk * C + 4 * (lane % Q));
       const int L[4] = {lv.x, lv.y, lv.z, lv.w};
+      const unsigned live = (L[0] == SS_INF ? 1u : 0u) | (L[1] == SS_INF ? 2u : 0u) |
+                            (L[2] == SS_INF ? 4u : 0u) | (L[3] == SS_INF ? 8u : 0u);
       int first[4] = {-1, -1, -1, -1};
       float sum[4] = {0.f, 0.f, 0.f, 0.f};
       bool need = true;
@@ -403,7 +412,7 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_pull(Dev d, int variant,
         }
 #pragma unroll
         for (int u = 0; u < PULL_STEP; ++u)
-          if (q0 + 32 * u < nq) scan_quad<SR>(d, sm, sbits, gbm, c[u], first, sum);  // warp-uniform
+          if (q0 + 32 * u < nq) scan_quad<SR>(d, sm, sbits, gbm, c[u], first, sum, live);  // warp-uniform
         if (MODE == MODE_FILTERED) {  // a row is done once visited or (not real) hit
           need = false;
 #pragma unroll
