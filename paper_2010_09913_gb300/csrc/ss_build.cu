@@ -565,6 +565,8 @@ static ss_status alloc_state(slimsell_graph* h) {
   if ((s = dmalloc(h, (void**)&h->feats, sizeof(float) * SS_SELECTOR_FEATURES * (size_t)h->iter_cap)) != SS_OK)
     return s;
   if ((s = dmalloc(h, (void**)&h->iters, sizeof(ss_iter_stats) * (size_t)h->iter_cap)) != SS_OK) return s;
+  if ((s = dmalloc(h, (void**)&h->lstat, sizeof(unsigned long long) * SS_LSTAT * (size_t)h->iter_cap)) != SS_OK)
+    return s;
   SS_CUDA(cudaMemset(h->arrive, 0, sizeof(unsigned) * ns));
   SS_CUDA(cudaMemset(h->fb[0], 0, sizeof(unsigned) * (size_t)h->fb_words));
   SS_CUDA(cudaMemset(h->fb[1], 0, sizeof(unsigned) * (size_t)h->fb_words));
@@ -584,7 +586,7 @@ void free_handle(slimsell_graph* h) {
                   h->lvl, h->act, h->fb[0], h->fb[1], h->fr, h->par, h->xacc, h->xpar,
                   h->arrive, h->ctl, h->iters, h->units, h->pbest,
                   h->psum, h->touched, h->qlist[0], h->qlist[1], h->qdeg[0], h->qdeg[1], h->qbase[0],
-                  h->qbase[1], h->qorig[0], h->qorig[1], h->qovf, h->qovf_n, h->mlp, h->feats, h->mF[0],
+                  h->qbase[1], h->qorig[0], h->qorig[1], h->qovf, h->qovf_n, h->lstat, h->mlp, h->feats, h->mF[0],
                   h->mF[1], h->mV, h->mxacc, h->mroots};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -627,7 +629,7 @@ ss::Dev slimsell_graph::dev() const {
   d.local_max_nf = (long long)local_cluster * SS_LOCAL_SLICE;
   d.local_max_e = (long long)local_cluster * SS_LOCAL_EDGES_PER_CTA;
   d.nnz = nnz; d.total_slots = slots; d.reach_cap = (unsigned long long)n;
-  d.ctl = ctl; d.iters = iters; d.iter_cap = iter_cap;
+  d.ctl = ctl; d.iters = iters; d.iter_cap = iter_cap; d.lstat = lstat;
   return d;
 }
 

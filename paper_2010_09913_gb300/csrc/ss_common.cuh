@@ -24,6 +24,7 @@
 #define SS_LOCAL_SLICE 4096
 #define SS_LOCAL_EDGES_PER_CTA 8192
 #define SS_LOCAL_CLUSTER_MAX 16
+#define SS_LSTAT 8  // words per level in lstat
 #define SS_LOCAL_LIST_CAP (SS_LOCAL_CLUSTER_MAX * SS_LOCAL_EDGES_PER_CTA)
 
 namespace ss {
@@ -111,6 +112,7 @@ struct Dev {
   unsigned long long reach_cap;  // most reached units a correct run can count (n, or n * k)
   Ctl* ctl;
   ss_iter_stats* iters; // [iter_cap]
+  unsigned long long* lstat;  // [iter_cap][LSTAT] cluster push: per-level totals for the features
   int iter_cap;
 };
 
@@ -167,6 +169,7 @@ struct slimsell_graph {
   ss::Ctl* ctl = nullptr;
   ss::Ctl* h_ctl = nullptr;  // pinned host copy
   ss_iter_stats* iters = nullptr;
+  unsigned long long* lstat = nullptr;
   int iter_cap = 0;
   long long device_bytes = 0;
   // last run

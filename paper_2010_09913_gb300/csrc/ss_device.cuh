@@ -140,6 +140,50 @@ __device__ __forceinline__ void finish_iteration_block(const Dev& d, unsigned lo
   }
 }
 
+// Selector features of iteration c->k (statistics of the frontier f_{k-1} and
+// the state), logged before every iteration; the 16-64-64-4 MLP reads them.
+// fp32 throughout: double-precision transcendentals are very slow on this GPU.
+__device__ __forceinline__ float feat_lg(float x) { return __log2f(1.0f + fmaxf(x, 0.0f)); }
+
+__device__ __forceinline__ void features_of(const Dev& d, int k, unsigned long long prev_new,
+                                            unsigned long long prev_deg, unsigned long long reached,
+                                            unsigned long long reached_deg, unsigned long long prev_active,
+                                            unsigned long long prev_slots, unsigned prev_maxdeg,
+                                            unsigned long long prev2_new, bool first, float* f) {
+  const float n = (float)d.n, nnz = (float)(d.nnz > 0 ? d.nnz : 1);
+  const float nf = (float)prev_new, mf = (float)prev_deg;
+  const float unv = (float)((unsigned long long)d.n - reached);
+  const float mu = (float)((unsigned long long)d.nnz - reached_deg);  // unexplored edge endpoints
+  f[0] = feat_lg(nf) / 32.f;
+  f[1] = nf / n;
+  f[2] = feat_lg(mf) / 32.f;
+  f[3] = mf / nnz;
+  f[4] = feat_lg(unv) / 32.f;
+  f[5] = unv / n;
+  f[6] = first ? 1.f : (float)prev_active / (float)(d.n_c > 0 ? d.n_c : 1);
+  f[7] = first ? 1.f : (float)prev_slots / (float)(d.total_slots > 0 ? d.total_slots : 1);
+  f[8] = (float)k / 32.f;
+  f[9] = (float)k / (float)(k + 1);
+  f[10] = feat_lg(mf / fmaxf(nf, 1.f)) / 32.f;
+  f[11] = feat_lg((float)prev_maxdeg) / 32.f;
+  f[12] = feat_lg(mu) / 32.f;
+  f[13] = feat_lg(n) / 32.f;
+  f[14] = feat_lg(nnz) / 32.f;
+  f[15] = feat_lg(nf / fmaxf((float)prev2_new, 1.f)) / 32.f;
+}
+
+__device__ __forceinline__ void compute_features(const Dev& d, const Ctl* c, float* f) {
+  features_of(d, c->k, c->prev_new, c->prev_deg, c->reached, c->reached_deg, c->prev_active, c->prev_slots,
+              c->prev_maxdeg, c->prev2_new, c->prev_variant < 0, f);
+}
+
+// Write the features of iteration k into d.feats (one thread).
+__device__ __forceinline__ void store_features(const Dev& d, int k, const float* f) {
+  if (k >= d.iter_cap) return;
+#pragma unroll
+  for (int i = 0; i < SS_SELECTOR_FEATURES; ++i) d.feats[(size_t)k * SS_SELECTOR_FEATURES + i] = f[i];
+}
+
 // Root state and control block of a new single-source run (one thread).
 __device__ __forceinline__ void init_root_state(const Dev& d, int root) {
   const int r = d.invperm[root];

@@ -315,6 +315,85 @@ __device__ __forceinline__ int share_owner(long long at, long long total, int lg
   return r;
 }
 
+// Selector features of the iterations after levels k0 .. k1 run in this launch
+// (the decide kernel did not run before them), from the per-level totals the
+// launch recorded; rank 0's threads, one level each, when the launch ends.
+__device__ __forceinline__ void local_features(const Dev& d, LocalSmem& S, cg::cluster_group& cl, int k0,
+                                               int k1) {
+  __syncthreads();  // the last level's totals are in place
+  if (cl.block_rank() != 0) return;
+  for (int k = k0 + (int)threadIdx.x; k <= k1 && k + 1 < d.iter_cap; k += LOCAL_THREADS) {
+    const unsigned long long* ls = d.lstat + (size_t)k * SS_LSTAT;
+    float f[SS_SELECTOR_FEATURES];
+    features_of(d, k + 1, ls[0], ls[1], ls[4], ls[5], 0ull, ls[3], (unsigned)ls[2], ls[6], false, f);
+    store_features(d, k + 1, f);
+  }
+}
+
+// One scatter pass of the cluster push: thread tid takes edges [ea, ea + per) of
+// the slice (per <= B), finds their rows by one binary search and a forward walk,
+// loads the neighbours, and claims each with one atomicMax (all B in flight
+// before any result is used); one atomicMax both claims a vertex (old value -1),
+// keeps the largest-id parent and tells visited vertices apart (their slot holds
+// SS_PBEST_VISITED, which no id exceeds).
+template <int SR, int C, int B>
+__device__ __forceinline__ void local_scatter(const Dev& d, LocalSmem& S, int p0, int p1, int ns, int e0,
+                                              int per, int Es, int tid) {
+  const int* sid = S.sid[p1];
+  const int ea = e0 + tid * per;
+  const int eb = min(ea + per, Es);
+  int i = 0;
+  if (ea < eb) {  // largest i with pref[i] <= ea
+    int lo_ = 0, hi_ = ns - 1;
+    while (lo_ < hi_) {
+      const int mid = (lo_ + hi_ + 1) >> 1;
+      if (S.pref[mid] <= ea) lo_ = mid;
+      else hi_ = mid - 1;
+    }
+    i = lo_;
+  }
+  int src[B], v[B];
+  float fu[B];  // real semiring: the source's value, loaded with the neighbour
+#pragma unroll
+  for (int q = 0; q < B; ++q) {
+    const int e = ea + q;
+    src[q] = -1;
+    v[q] = -1;
+    fu[q] = 0.0f;
+    if (e < eb) {
+      while (i + 1 < ns && S.pref[i + 1] <= e) ++i;
+      src[q] = i;
+      v[q] = __ldg(d.col + S.base[i] + (long long)(e - S.pref[i]) * C);
+      if (SR == SS_REAL) fu[q] = __ldcg(d.fr + sid[i]);  // written during this launch: past L1
+    }
+  }
+  int old[B];
+#pragma unroll
+  for (int q = 0; q < B; ++q) {
+    old[q] = SS_PBEST_VISITED;
+    if (v[q] >= 0) old[q] = atomicMax(d.pbest + v[q], S.orig[src[q]]);
+  }
+  if (SR == SS_REAL) {
+#pragma unroll
+    for (int q = 0; q < B; ++q)
+      if (old[q] != SS_PBEST_VISITED) atomicAdd(d.psum + v[q], fu[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < B; ++q) {
+    if (old[q] < 0) {  // first discoverer: this CTA owns the vertex
+      const int idx = atomicAdd(&S.nnew, 1);
+      if (idx < LOCAL_NEWCAP) {
+        S.nid[idx] = v[q];
+      } else {  // past this CTA's list (skewed slices): the shared overflow list
+        atomicAdd(&S.novf, 1);
+        const unsigned long long o = atomicAdd(d.qovf_n + p0, 1ull);
+        if (o < (unsigned long long)SS_LOCAL_LIST_CAP) d.qovf[o] = v[q];
+        else atomicOr(&S.ctl.error, 16);  // cannot happen: new vertices <= E <= cap
+      }
+    }
+  }
+}
+
 template <int SR, int C>
 __global__ void __launch_bounds__(LOCAL_THREADS, 1) k_push_local(Dev d, IterLaunch il, int max_levels) {
   constexpr int BATCH = (SR == SS_REAL) ? LOCAL_BATCH / 2 : LOCAL_BATCH;  // registers
@@ -338,6 +417,7 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) k_push_local(Dev d, IterLaun
   cl.sync();  // every CTA holds its copy before CTA 0 can write the block back
   if (S.ctl.done) return;  // the same in every CTA; no shared memory was shared yet
   int k = S.ctl.k;
+  const int k0 = k;  // first level of this launch (its features came from the decide kernel)
   const bool have_list = S.ctl.list_level == k - 1;
   long long nf = (long long)(have_list ? S.ctl.qlen[(k - 1) & 1] : S.ctl.qprep);
   long long E = (long long)S.ctl.prev_deg;  // edges of the level-(k-1) frontier
@@ -382,8 +462,10 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) k_push_local(Dev d, IterLaun
   cl.sync();  // the first slices, with the units of long rows, are in place
   int ns_prev = 0;  // entries of S.sid[k&1]: this CTA's slice of level k-2 (after the first level)
   unsigned long long reached = S.ctl.reached;  // every thread tracks the stop condition
+  unsigned long long reached_deg = S.ctl.reached_deg;
   for (int lev = 0;; ++lev) {
     if (lev > 0 && (lev >= max_levels || !local_fits(d, (unsigned long long)nf, (unsigned long long)E))) {
+      local_features(d, S, cl, k0, k - 1);
       if (tid == 0) {  // hand the level-(k-1) list back
         S.ctl.list_level = k - 1;
         S.ctl.list_prev_ok = 1;
@@ -462,62 +544,14 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) k_push_local(Dev d, IterLaun
     }
     __syncthreads();
     const int Es = S.es;
-    // ---- scatter: each thread a contiguous run of at most BATCH edges per pass ----
-    const int* sid = S.sid[p1];
+    // ---- scatter: each thread a contiguous run of at most BATCH edges per pass
+    // (a 4-edge batch when that covers the slice: fewer idle unrolled steps) ----
     for (int e0 = 0; e0 < Es; e0 += LOCAL_THREADS * BATCH) {
       const int per = min(BATCH, (Es - e0 + LOCAL_THREADS - 1) / LOCAL_THREADS);
-      const int ea = e0 + tid * per;
-      const int eb = min(ea + per, Es);
-      int i = 0;
-      if (ea < eb) {  // largest i with pref[i] <= ea
-        int lo_ = 0, hi_ = ns - 1;
-        while (lo_ < hi_) {
-          const int mid = (lo_ + hi_ + 1) >> 1;
-          if (S.pref[mid] <= ea) lo_ = mid;
-          else hi_ = mid - 1;
-        }
-        i = lo_;
-      }
-      int src[BATCH], v[BATCH];
-#pragma unroll
-      for (int q = 0; q < BATCH; ++q) {
-        const int e = ea + q;
-        src[q] = -1;
-        v[q] = -1;
-        if (e < eb) {
-          while (i + 1 < ns && S.pref[i + 1] <= e) ++i;
-          src[q] = i;
-          v[q] = __ldg(d.col + S.base[i] + (long long)(e - S.pref[i]) * C);
-        }
-      }
-      // one atomicMax per candidate claims it, finds the largest-id parent and
-      // tells visited vertices apart (their slot holds SS_PBEST_VISITED, which no
-      // id exceeds); all atomics of the batch are in flight before a result is used
-      int old[BATCH];
-#pragma unroll
-      for (int q = 0; q < BATCH; ++q) {
-        old[q] = SS_PBEST_VISITED;
-        if (v[q] >= 0) old[q] = atomicMax(d.pbest + v[q], S.orig[src[q]]);
-      }
-      if (SR == SS_REAL) {  // values of this launch's vertices are read past L1
-#pragma unroll
-        for (int q = 0; q < BATCH; ++q)
-          if (old[q] != SS_PBEST_VISITED) atomicAdd(d.psum + v[q], __ldcg(d.fr + sid[src[q]]));
-      }
-#pragma unroll
-      for (int q = 0; q < BATCH; ++q) {
-        if (old[q] < 0) {  // first discoverer: this CTA owns the vertex
-          const int idx = atomicAdd(&S.nnew, 1);
-          if (idx < LOCAL_NEWCAP) {
-            S.nid[idx] = v[q];
-          } else {  // past this CTA's list (skewed slices): the shared overflow list
-            atomicAdd(&S.novf, 1);
-            const unsigned long long o = atomicAdd(d.qovf_n + p0, 1ull);
-            if (o < (unsigned long long)SS_LOCAL_LIST_CAP) d.qovf[o] = v[q];
-            else atomicOr(&S.ctl.error, 16);  // cannot happen: new vertices <= E <= cap
-          }
-        }
-      }
+      if (per <= 4)
+        local_scatter<SR, C, 4>(d, S, p0, p1, ns, e0, per, Es, tid);
+      else
+        local_scatter<SR, C, BATCH>(d, S, p0, p1, ns, e0, per, Es, tid);
     }
     __syncthreads();
     if (tid < G) {  // tell every CTA how many vertices this one found
@@ -644,11 +678,21 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) k_push_local(Dev d, IterLaun
       S.ctl.list_level = k;
       S.ctl.list_prev_ok = 1;
     }
+    reached_deg += td;
+    if (rank == 0 && wid == LOCAL_THREADS / 32 - 1 && lane < 7 && k < d.iter_cap) {
+      // the totals the next level's selector features come from (computed at exit)
+      const unsigned long long v = lane == 0 ? (unsigned long long)tot : lane == 1 ? td
+                                 : lane == 2 ? (unsigned long long)tm : lane == 3 ? (unsigned long long)E
+                                 : lane == 4 ? reached : lane == 5 ? reached_deg : (unsigned long long)nf;
+      d.lstat[(size_t)k * SS_LSTAT + lane] = v;
+    }
     if (stop) {
+      local_features(d, S, cl, k0, k - 1);
       local_exit(S, c, il, 0u, cl);
       return;
     }
     if (!next_here || dropped) {  // the next frontier does not fit: hand back before using it
+      local_features(d, S, cl, k0, k);
       ++k;
       if (tid == 0) {
         S.ctl.list_level = k - 1;

@@ -26,35 +26,6 @@ static_assert(N_PARAMS == SS_SELECTOR_PARAMS, "selector parameter count");
 
 constexpr int PUSH_UNIT_SEL = 256;  // must match the push kernels' unit size
 
-// fp32 throughout: double-precision transcendentals are very slow on this GPU.
-__device__ __forceinline__ float lg(float x) { return __log2f(1.0f + fmaxf(x, 0.0f)); }
-
-// Features of iteration k (statistics of the frontier f_{k-1} and the state).
-__device__ void compute_features(const Dev& d, const Ctl* c, float* f) {
-  const float n = (float)d.n, nnz = (float)(d.nnz > 0 ? d.nnz : 1);
-  const float nf = (float)c->prev_new, mf = (float)c->prev_deg;
-  const float unv = (float)((unsigned long long)d.n - c->reached);
-  const float mu = (float)((unsigned long long)d.nnz - c->reached_deg);  // unexplored edge endpoints
-  const int k = c->k;
-  const bool first = c->prev_variant < 0;
-  f[0] = lg(nf) / 32.f;
-  f[1] = nf / n;
-  f[2] = lg(mf) / 32.f;
-  f[3] = mf / nnz;
-  f[4] = lg(unv) / 32.f;
-  f[5] = unv / n;
-  f[6] = first ? 1.f : (float)c->prev_active / (float)(d.n_c > 0 ? d.n_c : 1);
-  f[7] = first ? 1.f : (float)c->prev_slots / (float)(d.total_slots > 0 ? d.total_slots : 1);
-  f[8] = (float)k / 32.f;
-  f[9] = (float)k / (float)(k + 1);
-  f[10] = lg(mf / fmaxf(nf, 1.f)) / 32.f;
-  f[11] = lg((float)c->prev_maxdeg) / 32.f;
-  f[12] = lg(mu) / 32.f;
-  f[13] = lg(n) / 32.f;
-  f[14] = lg(nnz) / 32.f;
-  f[15] = lg(nf / fmaxf((float)c->prev2_new, 1.f)) / 32.f;
-}
-
 // Frontier-size rule (top-down / bottom-up switching with alpha = 14, beta = 24).
 __device__ int heuristic_variant(const Dev& d, const Ctl* c) {
   const unsigned long long nf = c->prev_new, mf = c->prev_deg;
