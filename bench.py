@@ -182,7 +182,8 @@ def run_reference(args, world, rank, pg):
         return
     g = gg.kronecker(args.scale, seed=1)
     roots = gg.roots(g, args.roots, seed=2)
-    per_step = max(10.0, min(30.0, 150.0 / max(1, args.steps + args.warmup)))
+    per_step = args.ref_seconds if args.ref_seconds is not None else \
+        max(10.0, min(30.0, 150.0 / max(1, args.steps + args.warmup)))
     import oracle
     oracle.build()
     idx = 0
@@ -524,6 +525,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-scale24", action="store_true")
     ap.add_argument("--no-high-diameter", action="store_true")
+    ap.add_argument("--ref-seconds", type=float, default=None,
+                    help="reference arm: seconds of oracle work per step (default 10-30)")
     ap.add_argument("--only", choices=["high-diameter"], default=None,
                     help="run one section alone and print it (profiling runs)")
     ap.add_argument("--host-loop", action="store_true",
