@@ -385,7 +385,8 @@ def batched_graphs(ss, torch, ngraphs, stream, dev):
 
 def roofline_at_scale(ss, torch, scale, nroots, split_w, stream, dev):
     """Plain single-source SlimSell BFS (SlimWork + SlimChunk) at a larger scale:
-    iteration-kernel GB/s from per-launch CUDA events, and whole-run GTEPS."""
+    iteration-kernel GB/s from per-launch CUDA events, and whole-run GTEPS; then
+    bit-packed multi-source BFS with 64, 256 and 1024 roots on the same graph."""
     g = gg.kronecker(scale, seed=1)
     roots = gg.roots(g, nroots, seed=2)
     rp_d = torch.from_numpy(g.row_ptr).to(dev)
@@ -419,6 +420,24 @@ def roofline_at_scale(ss, torch, scale, nroots, split_w, stream, dev):
                    "gteps_slimwork": edges / (ms / 1000.0) / 1e9}
         gte, _ = time_policy(ss, torch, h, roots, ss.V_HEURISTIC, stream, 4 * edges)
         out[sr]["gteps_heuristic_all4"] = gte
+    # bit-packed multi-source BFS on the same graph (k seeded roots at once, k x n
+    # int32 distances written), against the single-source runs above
+    for k in (64, 256, 1024):
+        mroots = gg.roots(g, k, seed=20 + k)
+        r_d = torch.from_numpy(mroots).to(dev)
+        dist = torch.empty((g.n, k), dtype=torch.int32, device=dev)
+        ss.slimsell_bfs_multi(h, r_d, ss.V_SLIMWORK, dist, stream)  # warm-up
+        st, _ = ss.slimsell_get_run_stats(h)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        ss.slimsell_bfs_multi(h, r_d, ss.V_SLIMWORK, dist, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[f"multi_{k}"] = {"gteps": (st.reached_degree // 2) / (ms / 1000.0) / 1e9, "ms": ms}
+        del dist
     ss.slimsell_destroy(h)
     return out
 
