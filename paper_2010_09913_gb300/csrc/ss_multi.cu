@@ -12,11 +12,22 @@
 // words of the neighbour (one W*8-byte segment).  SlimWork skips chunks whose
 // rows have every source visited; split chunks (SlimChunk) combine partial ORs
 // with 64-bit atomicOr and the last arriving block post-processes.
+//
+// The gathers are most of the traffic (W*8 bytes per slot), so they are
+// skipped where they cannot matter: a one-bit-per-vertex summary of the
+// frontier (bit u set iff some source has u in its frontier, kept in the
+// single-source frontier bitmaps fb[], unused here) is tested first, and a
+// thread whose 64 sources have all visited its row gathers nothing.
 #include <vector>
 
 #include "ss_device.cuh"
 
 namespace ss {
+
+#ifndef SS_MULTI_BATCH
+#define SS_MULTI_BATCH 8
+#endif
+constexpr int MULTI_BATCH = SS_MULTI_BATCH;  // columns per thread in flight
 
 struct MultiDev {
   Dev d;
@@ -28,6 +39,15 @@ struct MultiDev {
   int k;
 };
 
+// The C summary bits of one chunk (bit l = row l) into the bitmap.
+template <int C>
+__device__ __forceinline__ void store_summary(unsigned* fa, int chunk, unsigned lo, unsigned hi) {
+  if (C == 8) reinterpret_cast<unsigned char*>(fa)[chunk] = (unsigned char)lo;
+  else if (C == 16) reinterpret_cast<unsigned short*>(fa)[chunk] = (unsigned short)lo;
+  else if (C == 32) fa[chunk] = lo;
+  else reinterpret_cast<uint2*>(fa)[chunk] = make_uint2(lo, hi);
+}
+
 template <int C, int W, bool SLIMWORK>
 __global__ void __launch_bounds__(C * W) k_multi_pull(MultiDev m, IterLaunch il) {
   constexpr int T = C * W;
@@ -38,7 +58,10 @@ __global__ void __launch_bounds__(C * W) k_multi_pull(MultiDev m, IterLaunch il)
   const int tid = threadIdx.x, r = tid / W, w = tid % W;
   const unsigned long long* Fp = m.F[(level - 1) & 1];
   unsigned long long* Fn = m.F[level & 1];
+  const unsigned* FAp = d.fb[(level - 1) & 1];  // frontier summary, one bit per row
+  unsigned* FAn = d.fb[level & 1];
   __shared__ int s_flag;
+  __shared__ unsigned s_fa[2];
   unsigned long long nw = 0, deg = 0, slots = 0, act = 0;
   unsigned maxdeg = 0;
   for (int it = blockIdx.x; it < d.n_items; it += gridDim.x) {
@@ -51,29 +74,36 @@ __global__ void __launch_bounds__(C * W) k_multi_pull(MultiDev m, IterLaunch il)
       if (a != 1) {
         if (a >= 2 && item.y == 0) {
           Fn[row * W + w] = 0ull;  // f_k is zero on a finished chunk
-          if (tid == 0) d.act[chunk] = (a == 3) ? 2 : 0;
+          if (tid == 0) {
+            store_summary<C>(FAn, chunk, 0u, 0u);
+            d.act[chunk] = (a == 3) ? 2 : 0;
+          }
         }
         continue;
       }
     }
     const long long start = d.cs[chunk] + (long long)item.y * C;
     const int ncol = item.z - item.y;
+    const unsigned long long vold0 = m.V[row * W + w];
+    const bool want = vold0 != ~0ull;  // some of this word's sources still miss the row
     unsigned long long acc = 0ull;
     int j = 0;
-    for (; j + 4 <= ncol; j += 4) {
-      const int c0 = __ldcs(d.col + start + (long long)(j + 0) * C + r);
-      const int c1 = __ldcs(d.col + start + (long long)(j + 1) * C + r);
-      const int c2 = __ldcs(d.col + start + (long long)(j + 2) * C + r);
-      const int c3 = __ldcs(d.col + start + (long long)(j + 3) * C + r);
-      const unsigned long long f0 = c0 >= 0 ? __ldg(Fp + (long long)c0 * W + w) : 0ull;
-      const unsigned long long f1 = c1 >= 0 ? __ldg(Fp + (long long)c1 * W + w) : 0ull;
-      const unsigned long long f2 = c2 >= 0 ? __ldg(Fp + (long long)c2 * W + w) : 0ull;
-      const unsigned long long f3 = c3 >= 0 ? __ldg(Fp + (long long)c3 * W + w) : 0ull;
-      acc |= f0 | f1 | f2 | f3;
+    for (; j + MULTI_BATCH <= ncol; j += MULTI_BATCH) {
+      int cc[MULTI_BATCH];
+#pragma unroll
+      for (int q = 0; q < MULTI_BATCH; ++q) cc[q] = __ldcs(d.col + start + (long long)(j + q) * C + r);
+      unsigned hit[MULTI_BATCH];
+#pragma unroll
+      for (int q = 0; q < MULTI_BATCH; ++q)
+        hit[q] = (want && cc[q] >= 0) ? (__ldg(FAp + (cc[q] >> 5)) >> (cc[q] & 31)) & 1u : 0u;
+#pragma unroll
+      for (int q = 0; q < MULTI_BATCH; ++q)
+        if (hit[q]) acc |= __ldg(Fp + (long long)cc[q] * W + w);
     }
     for (; j < ncol; ++j) {
       const int cc = __ldcs(d.col + start + (long long)j * C + r);
-      if (cc >= 0) acc |= __ldg(Fp + (long long)cc * W + w);
+      if (want && cc >= 0 && ((__ldg(FAp + (cc >> 5)) >> (cc & 31)) & 1u))
+        acc |= __ldg(Fp + (long long)cc * W + w);
     }
     if (tid == 0) slots += (unsigned long long)ncol * C;
     if (item.w >= 0) {  // SlimChunk: OR the partial rows, last block to arrive post-processes
@@ -92,8 +122,11 @@ __global__ void __launch_bounds__(C * W) k_multi_pull(MultiDev m, IterLaunch il)
       *xa = 0ull;
       if (tid == 0) d.arrive[item.w] = 0u;
     }
-    const unsigned long long vold = m.V[row * W + w];
+    if (tid == 0) s_fa[0] = s_fa[1] = 0u;
+    __syncthreads();
+    const unsigned long long vold = vold0;
     const unsigned long long nb = acc & ~vold;
+    if (nb) atomicOr(&s_fa[r >> 5], 1u << (r & 31));
     if (nb) {
       m.V[row * W + w] = vold | nb;
       const int pc = __popcll(nb);
@@ -114,6 +147,7 @@ __global__ void __launch_bounds__(C * W) k_multi_pull(MultiDev m, IterLaunch il)
     Fn[row * W + w] = nb;
     const int left = __syncthreads_or((vold | nb) != ~0ull);
     if (tid == 0) {
+      store_summary<C>(FAn, chunk, s_fa[0], s_fa[1]);
       d.act[chunk] = left ? 1 : 3;
       act += 1;
     }
@@ -144,6 +178,10 @@ __global__ void k_multi_init(MultiDev m, int W) {
   }
   for (long long i = t0; i < d.n_c; i += stride) d.act[i] = 1;
   for (long long s = t0; s < (long long)d.n_split * d.C * W; s += stride) m.xacc[s] = 0ull;
+  for (long long i = t0; i < d.fb_words; i += stride) {
+    d.fb[0][i] = 0u;
+    d.fb[1][i] = 0u;
+  }
 }
 
 __global__ void k_multi_roots(MultiDev m, int W) {
@@ -154,6 +192,7 @@ __global__ void k_multi_roots(MultiDev m, int W) {
     const unsigned long long bit = 1ull << (s & 63);
     atomicOr(m.V + r * W + s / 64, bit);
     atomicOr(m.F[0] + r * W + s / 64, bit);
+    atomicOr(d.fb[0] + (r >> 5), 1u << (r & 31));
     if (m.dist) m.dist[(long long)v * m.k + s] = 0;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
