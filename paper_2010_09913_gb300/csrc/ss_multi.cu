@@ -18,6 +18,8 @@
 // frontier (bit u set iff some source has u in its frontier, kept in the
 // single-source frontier bitmaps fb[], unused here) is tested first, and a
 // thread whose 64 sources have all visited its row gathers nothing.
+#include <algorithm>
+#include <cstdint>
 #include <vector>
 
 #include "ss_device.cuh"
@@ -25,9 +27,12 @@
 namespace ss {
 
 #ifndef SS_MULTI_BATCH
-#define SS_MULTI_BATCH 8
+#define SS_MULTI_BATCH 4
 #endif
 constexpr int MULTI_BATCH = SS_MULTI_BATCH;  // columns per thread in flight
+#ifndef SS_MULTI_BLOCKS_PER_SM
+#define SS_MULTI_BLOCKS_PER_SM 0  // resident blocks per SM (0: as many as fit)
+#endif
 
 struct MultiDev {
   Dev d;
@@ -35,9 +40,29 @@ struct MultiDev {
   unsigned long long* V;
   unsigned long long* xacc;  // [n_split][C][W]
   int* dist;                 // [n][k] in original vertex order, or NULL
+  int vec_dist;              // k % 4 == 0 and dist 16-byte aligned: 16-byte group writes
   const int* roots;          // [k]
   int k;
 };
+
+// Distances of the new sources (bits of nb) of one 64-source word, in 16-byte
+// groups of 4: a group with no earlier discovery (bits of vold) still holds -1
+// everywhere and is written whole; otherwise it is read first.  Kept out of line
+// so that the gather loop's register allocation does not depend on it.
+__device__ __noinline__ void write_levels_vec(int* out, unsigned long long nb, unsigned long long vold,
+                                             int level) {
+  for (int gi = 0; gi < 16; ++gi) {
+    const unsigned ng = (unsigned)(nb >> (4 * gi)) & 0xFu;
+    if (!ng) continue;
+    int4* q = reinterpret_cast<int4*>(out) + gi;
+    int4 v = ((unsigned)(vold >> (4 * gi)) & 0xFu) ? *q : make_int4(-1, -1, -1, -1);
+    if (ng & 1u) v.x = level;
+    if (ng & 2u) v.y = level;
+    if (ng & 4u) v.z = level;
+    if (ng & 8u) v.w = level;
+    *q = v;
+  }
+}
 
 // The C summary bits of one chunk (bit l = row l) into the bitmap.
 template <int C>
@@ -136,11 +161,15 @@ __global__ void __launch_bounds__(C * W) k_multi_pull(MultiDev m, IterLaunch il)
       maxdeg = max(maxdeg, (unsigned)dv);
       if (m.dist) {
         int* out = m.dist + (long long)d.perm[row] * m.k + 64 * w;
-        unsigned long long b = nb;
-        while (b) {
-          const int s = __ffsll((long long)b) - 1;
-          b &= b - 1;
-          out[s] = level;
+        if (m.vec_dist) {
+          write_levels_vec(out, nb, vold, level);
+        } else {
+          unsigned long long b = nb;
+          while (b) {
+            const int s = __ffsll((long long)b) - 1;
+            b &= b - 1;
+            out[s] = level;
+          }
         }
       }
     }
@@ -228,6 +257,7 @@ static ss_status launch_multi_cw(const slimsell_graph* h, const MultiDev& m, boo
       int b = 0;
       if (slimwork) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_multi_pull<C, W, true>, C * W, 0);
       else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_multi_pull<C, W, false>, C * W, 0);
+      if (SS_MULTI_BLOCKS_PER_SM > 0) b = std::min(b, SS_MULTI_BLOCKS_PER_SM);
       g = (b > 0 ? b : 1) * h->num_sms;
     }
     if (slimwork) k_multi_pull<C, W, true><<<g, C * W, 0, st>>>(m, il);
@@ -323,6 +353,7 @@ extern "C" ss_status slimsell_bfs_multi(slimsell_handle h, const int32_t* d_root
   m.V = h->mV;
   m.xacc = h->mxacc;
   m.dist = d_dist;
+  m.vec_dist = (k % 4 == 0) && ((reinterpret_cast<uintptr_t>(d_dist) & 15u) == 0);
   m.roots = h->mroots;
   m.k = k;
   const bool prof = h->profiling != 0;

@@ -84,3 +84,21 @@ def test_kron22_multi_sampled():
         want = oracle.bfs_queue(g.row_ptr, g.col, int(roots[s]))
         np.testing.assert_array_equal(dist[:, s].cpu().numpy(), want)
     G.close()
+
+
+@pytest.mark.parametrize("offset", [0, 1])
+def test_distance_writes_aligned_and_not(offset):
+    """k = 100 (a multiple of 4): an aligned output takes 16-byte group writes, one
+    shifted by a single int32 takes per-entry writes; both equal the oracle."""
+    g = gg.kronecker(11, seed=4)
+    G = ss.SlimSellGraph.from_host(g.row_ptr, g.col, C=32, sigma=g.n, split_w=64)
+    roots = gg.roots(g, 100, seed=6)
+    buf = torch.full((g.n * 100 + 4,), 7, dtype=torch.int32, device="cuda")
+    dist = buf[offset:offset + g.n * 100].view(g.n, 100)
+    ss.slimsell_bfs_multi(G.h, torch.from_numpy(roots).cuda(), ss.V_SLIMWORK, dist)
+    torch.cuda.synchronize()
+    want = oracle.bfs_multi(g.row_ptr, g.col, roots)
+    np.testing.assert_array_equal(dist.cpu().numpy(), want.T)
+    rest = torch.cat([buf[:offset], buf[offset + g.n * 100:]]).cpu().numpy()
+    assert (rest == 7).all()  # nothing written outside the output
+    G.close()
