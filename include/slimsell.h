@@ -117,7 +117,10 @@ typedef struct {
  *   C          chunk height, one of 8, 16, 32, 64.
  *   sigma      sorting scope: rows are sorted by descending degree (ties by
  *              ascending id) inside windows of sigma consecutive vertices;
- *              sigma <= 1 keeps the input order, sigma >= n sorts globally.
+ *              sigma <= 1 keeps the input order, sigma > 1 is first rounded up
+ *              to a multiple of C (the paper takes sigma as a multiple of C,
+ *              Section IV; ss_info.sigma reports the value used), sigma >= n
+ *              sorts globally.
  *   split_w    SlimChunk width: chunks with more than split_w columns are split
  *              into ceil(cl / split_w) work items (Section III-D); 0 disables.
  * The call synchronises `stream` (it needs the layout size to allocate col).
@@ -236,7 +239,8 @@ ss_status slimsell_export_layout(slimsell_handle h, int32_t* d_perm, int32_t* d_
  * is a library convenience).  Writes perm[r] = the vertex placed at row
  * position r by the same ordering slimsell_build uses (descending degree inside
  * windows of sigma consecutive vertices, ties by ascending id; sigma <= 1 keeps
- * the input order), for r in [0, n).
+ * the input order), for r in [0, n).  sigma is used as given: slimsell_build
+ * first rounds its sigma up to a multiple of C, so pass that value to match it.
  *
  * For callers that must not allocate device memory: processes whose device
  * memory is fully reserved by another allocator, where cudaMalloc would fail,

@@ -158,7 +158,9 @@ def slimsell_layout(row_ptr, col, C: int, sigma: int, split_w: int = 0):
     """SlimSell layout by definition (Sections II-D, III-B, III-D).
 
     * Rows are sorted by descending degree inside windows [j*sigma, (j+1)*sigma),
-      ties by ascending vertex id; sigma <= 1 keeps the identity order.
+      ties by ascending vertex id; sigma <= 1 keeps the identity order, and any
+      other sigma is first rounded up to a multiple of C (the paper takes sigma
+      as a multiple of C, Section IV).
     * ``perm[r]`` = vertex stored at row position r; ``invperm[v]`` = its position.
     * Chunk i holds rows [i*C, (i+1)*C); rows beyond n are empty padding rows.
     * ``cl[i]`` = longest row of chunk i; ``cs`` = exclusive prefix sum of C*cl.
@@ -176,7 +178,8 @@ def slimsell_layout(row_ptr, col, C: int, sigma: int, split_w: int = 0):
     if sigma <= 1:
         perm = ids.copy()
     else:
-        window = ids // int(sigma)
+        sigma = -(-int(sigma) // C) * C  # rounded up to a multiple of C
+        window = ids // sigma
         perm = np.lexsort((ids, -deg, window))  # primary key: window, then -deg, then id
     invperm = np.empty(n, dtype=np.int64)
     invperm[perm] = ids

@@ -7,6 +7,7 @@
 //   5. column-major pack: col[cs_i + j*C + l] = invperm[j-th neighbour of row i*C+l,
 //      descending original id], or -1 for padding
 #include <cstdarg>
+#include <climits>
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -475,7 +476,7 @@ static ss_status build_impl(slimsell_graph* h, const long long* row_ptr, const i
   if (h->sigma <= 1) {
     k_identity<<<grid, 256, 0, st>>>(vals_a, n);
   } else {
-    const int sigma = h->sigma >= n ? n : h->sigma;
+    const int sigma = h->sigma >= n ? n : h->sigma;  // already a multiple of C (or >= n)
     const int dbits = bit_width((unsigned long long)h_maxdeg);
     const long long nwin = ((long long)n + sigma - 1) / sigma;
     const int wbits = bit_width((unsigned long long)(nwin - 1));
@@ -668,7 +669,8 @@ ss_status slimsell_build(const int64_t* d_row_ptr, const int32_t* d_col, int32_t
   h->n = n;
   h->nnz = nnz;
   h->C = C;
-  h->sigma = sigma;
+  // sigma > 1 is rounded up to a multiple of C (the paper takes it as one, Section IV)
+  h->sigma = sigma <= 1 ? 1 : (int)std::min<long long>(((long long)sigma + C - 1) / C * C, INT_MAX);
   h->split_w = split_w;
   h->n_c = (int)n_c;
   h->n_pad = (int)(n_c * C);

@@ -44,8 +44,26 @@ def test_sort_moves_hub_first():
     assert L["col"][:2].tolist() == [inv[4], inv[3]]
 
 
+def test_sigma_rounds_up_to_a_multiple_of_C():
+    """Section IV takes sigma as a multiple of C: any other sigma > 1 acts as the
+    next multiple (here 5 -> 8 and 9 -> 12 with C = 4); sigma = 1 keeps the order."""
+    g = gg.kronecker(9, seed=12)
+    for s, s_eff in [(5, 8), (9, 12), (8, 8)]:
+        a = oracle.slimsell_layout(g.row_ptr, g.col, C=4, sigma=s)
+        b = oracle.slimsell_layout(g.row_ptr, g.col, C=4, sigma=s_eff)
+        np.testing.assert_array_equal(a["perm"], b["perm"])
+        np.testing.assert_array_equal(a["col"], b["col"])
+    # by hand: degrees 2, 0, 1, 1; C = 2 and sigma = 3 give one window of 4
+    # vertices (not 3 + 1), so the order is 0, 2, 3, 1 (unrounded: 0, 2, 1, 3)
+    h = gg.from_edges(4, [(0, 2), (0, 3)])
+    L = oracle.slimsell_layout(h.row_ptr, h.col, C=2, sigma=3)
+    assert L["perm"].tolist() == [0, 2, 3, 1]
+
+
 def check_layout(g, C, sigma, split_w=0):
     L = oracle.slimsell_layout(g.row_ptr, g.col, C, sigma, split_w)
+    if sigma > 1:
+        sigma = -(-sigma // C) * C  # the window the layout uses
     n, deg = g.n, g.degrees()
     perm, inv, cl, cs, col = L["perm"], L["invperm"], L["cl"], L["cs"], L["col"]
     assert np.array_equal(np.sort(perm), np.arange(n))

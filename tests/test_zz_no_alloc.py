@@ -23,7 +23,8 @@ MAX_N = 1 << 19
 
 
 def reference_perm(g, sigma):
-    G = ss.SlimSellGraph.from_host(g.row_ptr, g.col, C=32, sigma=sigma, split_w=0)
+    # C = 8: every sigma below is a multiple of 8, so slimsell_build keeps it as given
+    G = ss.SlimSellGraph.from_host(g.row_ptr, g.col, C=8, sigma=sigma, split_w=0)
     perm = G.export_layout()["perm"][: g.n].cpu().numpy()
     G.close()
     return perm
