@@ -159,22 +159,77 @@ def sum_over_ranks(pg, x: float, device=None) -> float:
     return float(t.item())
 
 
-def cpu_oracle_sample(g, roots, budget_s: float):
-    """Time the oracle's plain CSR semiring BFS (all four semirings, DP parents)
-    on one core, root after root, until the budget is used."""
-    import oracle
+def _oracle_warm(_):
+    import oracle  # the import and library load, outside the timed rounds
     oracle.build()
-    edges, t_total, runs = 0, 0.0, 0
-    for r in roots:
-        for sr in SEMIRINGS:
+    time.sleep(0.2)  # hold this worker so that every worker gets one
+    return 0
+
+
+def _oracle_task(task):
+    """One oracle BFS in a worker process: (edges reached, seconds)."""
+    path, root, sr = task
+    import oracle
+    row_ptr = np.load(os.path.join(path, "row_ptr.npy"), mmap_mode="r")
+    col = np.load(os.path.join(path, "col.npy"), mmap_mode="r")
+    t0 = time.perf_counter()
+    dist = oracle.bfs_semiring(row_ptr, col, int(root), sr)[0]
+    dt = time.perf_counter() - t0
+    return oracle.reached_edges(row_ptr, dist), dt
+
+
+class OraclePool:
+    """The oracle's plain CSR semiring BFS run on the host cores, one serial BFS
+    per worker process (spawned, so no CUDA state is inherited); the CSR goes to
+    the workers through memory-mapped files."""
+
+    def __init__(self, g, workers: int):
+        import multiprocessing as mp
+        import tempfile
+        import oracle
+        oracle.build()
+        self.dir = tempfile.mkdtemp(prefix="ss_oracle_")
+        np.save(os.path.join(self.dir, "row_ptr.npy"), np.asarray(g.row_ptr))
+        np.save(os.path.join(self.dir, "col.npy"), np.asarray(g.col))
+        self.workers = max(1, workers)
+        self.pool = mp.get_context("spawn").Pool(self.workers)
+        self.pool.map(_oracle_warm, range(self.workers), chunksize=1)
+
+    def rounds(self, tasks, cpu_budget_s: float):
+        """Run tasks a round (one per worker) at a time until the CPU seconds reach
+        the budget (at least one round): (edges, wall seconds, cpu seconds, runs)."""
+        edges, wall, cpu, runs, i = 0, 0.0, 0.0, 0, 0
+        while runs == 0 or (cpu < cpu_budget_s and runs < 1_000_000):  # tasks cycle
+            batch = [tasks[(i + j) % len(tasks)] for j in range(self.workers)]
+            i += self.workers
             t0 = time.perf_counter()
-            dist, parent, _, _, _ = oracle.bfs_semiring(g.row_ptr, g.col, int(r), sr)
-            t_total += time.perf_counter() - t0
-            edges += oracle.reached_edges(g.row_ptr, dist)
-            runs += 1
-        if t_total >= budget_s:
-            break
-    return edges, t_total, runs
+            res = self.pool.map(_oracle_task, [(self.dir, r, sr) for r, sr in batch], chunksize=1)
+            wall += time.perf_counter() - t0
+            edges += sum(e for e, _ in res)
+            cpu += sum(t for _, t in res)
+            runs += len(res)
+        return edges, wall, cpu, runs
+
+    def close(self):
+        import shutil
+        self.pool.terminate()
+        shutil.rmtree(self.dir, ignore_errors=True)
+
+
+def oracle_workers() -> int:
+    return max(1, min(8, os.cpu_count() or 1))
+
+
+def cpu_oracle_sample(g, roots, cpu_budget_s: float):
+    """Time the oracle (all four semirings, DP parents) on the host cores over a
+    bounded sample of the workload's runs."""
+    pool = OraclePool(g, oracle_workers())
+    try:
+        tasks = [(int(r), sr) for r in roots for sr in SEMIRINGS]
+        edges, wall, cpu, runs = pool.rounds(tasks, cpu_budget_s)
+    finally:
+        pool.close()
+    return edges, wall, cpu, runs, pool.workers
 
 
 def run_reference(args, world, rank, pg):
@@ -184,34 +239,30 @@ def run_reference(args, world, rank, pg):
     roots = gg.roots(g, args.roots, seed=2)
     per_step = args.ref_seconds if args.ref_seconds is not None else \
         max(10.0, min(30.0, 150.0 / max(1, args.steps + args.warmup)))
-    import oracle
-    oracle.build()
-    idx = 0
-    times, edges_l = [], []
-    for s in range(args.warmup + args.steps):
-        edges, t_tot, runs = 0, 0.0, 0
-        while t_tot < per_step or runs == 0:
-            r = int(roots[idx % len(roots)])
-            idx += 1
-            for sr in SEMIRINGS:
-                t0 = time.perf_counter()
-                dist, _, _, _, _ = oracle.bfs_semiring(g.row_ptr, g.col, r, sr)
-                t_tot += time.perf_counter() - t0
-                edges += oracle.reached_edges(g.row_ptr, dist)
-                runs += 1
-        if s >= args.warmup:
-            times.append(t_tot)
-            edges_l.append(edges)
+    pool = OraclePool(g, oracle_workers())
+    tasks = [(int(r), sr) for r in roots for sr in SEMIRINGS]
+    times, edges_l, cpu_l = [], [], []
+    try:
+        for s in range(args.warmup + args.steps):
+            k = (s * pool.workers) % len(tasks)
+            edges, wall, cpu, runs = pool.rounds(tasks[k:] + tasks[:k], per_step)
+            if s >= args.warmup:
+                times.append(wall)
+                edges_l.append(edges)
+                cpu_l.append(cpu)
+    finally:
+        pool.close()
     value = sum(edges_l) / sum(times) / 1e9
     ms = 1000.0 * sum(times) / len(times)
-    sample = (f"oracle semiring BFS (plain CSR, fp64, serial C), all 4 semirings per root, "
-              f"~{per_step:.0f} s of roots per step on kronecker scale {args.scale}")
+    sample = (f"oracle semiring BFS (plain CSR, fp64, serial C per run), all 4 semirings per root, "
+              f"one run per worker process on {pool.workers} host cores, ~{per_step:.0f} CPU-seconds "
+              f"per step on kronecker scale {args.scale}")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GTEPS",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": workload_config(args, g),
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample, "value": value,
+            "cpu_baseline": {"kind": "oracle", "cores": pool.workers, "sample": sample, "value": value,
                              "unit": "GTEPS"},
             "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -662,6 +713,19 @@ def main():
                       "pull_bytes_per_run": b / (args.steps * len(roots)),
                       "whole_run_gbs": b / (ms / 1000.0) / 1e9,
                       "whole_run_hbm_frac": b / (ms / 1000.0) / 1e9 / hbm}
+    # Graph500 convention alongside the aggregate: the harmonic mean over roots of
+    # per-root GTEPS (each run timed alone with CUDA events, device-side loop)
+    ev_a = torch.cuda.Event(enable_timing=True)
+    ev_b = torch.cuda.Event(enable_timing=True)
+    for sr in SEMIRINGS:
+        inv = 0.0
+        for x in (x for x in runs if x["sr"] == sr):
+            ev_a.record(stream)
+            ss.slimsell_bfs(h, x["root"], SR_ID[sr], ss.V_SLIMWORK, dist, parent, stream)
+            ev_b.record(stream)
+            torch.cuda.synchronize()
+            inv += (ev_a.elapsed_time(ev_b) / 1000.0) / max(1, x["edges"])
+        per_sr[sr]["gteps_harmonic_mean_over_roots"] = len(roots) / inv / 1e9
     traffic = NCU_TRAFFIC.get(kernel_source_hash())
 
     line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world,
@@ -703,11 +767,13 @@ def main():
         torch.cuda.empty_cache()
         line["selector_heldout"] = selector_heldout(ss, torch, stream, dev, sel_w)
     if rank == 0 and world == 1 and not args.no_cpu:
-        edges, t_cpu, nruns = cpu_oracle_sample(g, roots, 20.0)
-        line["cpu_baseline"] = {"value": edges / t_cpu / 1e9, "unit": "GTEPS", "cores": 1,
+        edges, wall, cpu, nruns, workers = cpu_oracle_sample(g, roots, 20.0)
+        line["cpu_baseline"] = {"value": edges / wall / 1e9, "unit": "GTEPS", "cores": workers,
                                 "kind": "oracle",
                                 "sample": f"{nruns} runs (roots x 4 semirings) of the oracle's plain "
-                                          f"CSR semiring BFS on kronecker scale {args.scale}, serial"}
+                                          f"CSR semiring BFS on kronecker scale {args.scale}, one serial "
+                                          f"run per worker process, {cpu:.0f} CPU-seconds in "
+                                          f"{wall:.1f} s"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg is not None:
