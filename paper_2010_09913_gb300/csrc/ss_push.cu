@@ -160,19 +160,25 @@ __global__ void __launch_bounds__(PUSH_THREADS) k_push_post(Dev d, IterLaunch il
 // Cluster push for small frontiers: one thread-block cluster (16 CTAs of 1024
 // threads where the device can place it, else 8) runs level after level inside
 // one launch, with no kernel boundary and no bitmap walk per level.  The
-// frontier is a vertex list in global memory with, per vertex, what the scatter
-// needs (degree, start of its column-major row, original id); each CTA takes an
-// equal slice of it into shared memory, scatters over the slice's edges (each
-// thread a contiguous run: one binary search, then a forward walk), and keeps
-// the vertices it discovers.  A vertex belongs to the CTA whose atomicMax on
-// its parent slot returned the initial -1.  Two hardware cluster barriers per
-// level order the scatter before the post step (which reads the final parents)
-// and the post step before the next level; per-CTA counts and statistics are
-// read across the cluster from distributed shared memory.  Spreading the
-// random gathers and atomics over many SMs is what makes a level cheap: one
-// SM's L1 serves about one uncoalesced line per clock.  Every CTA keeps a copy
-// of the control block in shared memory, updated identically from the cluster
-// totals, so all CTAs take the same exits; CTA 0 writes it back at the end.
+// frontier is a vertex list; each CTA holds an equal share of it in shared
+// memory with, per entry, what the scatter needs (start of the row's edges in
+// col, edge count, original id).  The first level's share is loaded from the
+// global list; later shares are written straight into the owning CTA's shared
+// memory by the CTAs that discover the vertices (distributed shared memory),
+// rows longer than LOCAL_UNIT edges being cut into units spread round-robin
+// over the cluster.  Per level a CTA scatters over its share's edges (each
+// thread a contiguous run: one binary search, then a forward walk) and claims
+// each candidate with one atomicMax on its parent slot: the old value -1 makes
+// this CTA the vertex's owner, visited vertices hold SS_PBEST_VISITED (no id
+// is larger, so their slot never changes), and the slot ends with the largest
+// id among the frontier neighbours, the parent.  Two hardware cluster barriers
+// per level order the scatter before the post step (which reads the final
+// parents) and the post step before the next level; per-CTA counts and
+// statistics reach every CTA through distributed shared memory.  Spreading the
+// random accesses over many SMs is what makes a level cheap: one SM's L1
+// serves about one uncoalesced line per clock.  Every CTA keeps a copy of the
+// control block in shared memory, updated identically from the cluster totals,
+// so all CTAs take the same exits; CTA 0 writes it back at the end.
 // The cluster hands back to the iteration loop when the frontier outgrows
 // d.local_max_nf vertices or d.local_max_e edges, or after max_levels levels,
 // leaving the bitmaps and lists as the grid-wide variants and the next launch
