@@ -94,7 +94,9 @@ typedef struct {
   int64_t active_chunks;   /* chunks processed (not skipped)                          */
   int32_t variant;         /* variant actually executed (0 FULL, 1 SLIMWORK, 2 PUSH, 3 FILTERED,
                               SS_VARIANT_PUSH_LOCAL)                                     */
-  int32_t kernel_ns;       /* iteration kernel time in ns when profiling is on, else 0 */
+  int32_t kernel_ns;       /* iteration kernel time in ns when profiling is on, else 0;
+                              levels run inside one cluster-push launch are timed on
+                              the device, the launch's entry counted in its first  */
 } ss_iter_stats;
 
 /* Summary of the last slimsell_bfs call on a handle. */

@@ -678,8 +678,8 @@ static ss_status launch_iteration(const slimsell_graph* h, const Dev& d, int sr,
 }
 
 // Queue the kernels of one iteration of the given variant.  The cluster push
-// runs as many small levels as it can per launch, except under per-level
-// timing (profiling on), where it runs one.
+// runs as many small levels as it can per launch (under profiling it times each
+// level on the device).
 static ss_status launch_variant(const slimsell_graph* h, const Dev& d, int sr, int variant,
                                 const IterLaunch& il, cudaStream_t st) {
   switch (variant) {
@@ -687,7 +687,7 @@ static ss_status launch_variant(const slimsell_graph* h, const Dev& d, int sr, i
     case VAR_SLIMWORK: return launch_iteration(h, d, sr, MODE_SLIMWORK, il, st);
     case VAR_PUSH: return launch_push(h, d, sr, il, st);
     case VAR_PUSH_LOCAL:
-      return launch_push_local(h, d, sr, il, (il.use_cond || !h->profiling) ? (1 << 30) : 1, st);
+      return launch_push_local(h, d, sr, il, 1 << 30, st);
     default: return launch_iteration(h, d, sr, MODE_FILTERED, il, st);
   }
 }
@@ -898,6 +898,7 @@ ss_status slimsell_bfs(slimsell_handle h, int32_t root, int32_t semiring, int32_
         SS_CUDA(cudaStreamSynchronize(st));
         variant = h->h_ctl->variant;
       }
+      const int k_before = h->h_ctl->k;  // valid when the cluster push is chosen (adaptive)
       if (prof) SS_CUDA(cudaEventRecord(h->ev_a, st));
       s = launch_variant(h, d, semiring, variant, IterLaunch{variant, 0, 0}, st);
       if (s != SS_OK) return s;
@@ -909,6 +910,10 @@ ss_status slimsell_bfs(slimsell_handle h, int32_t root, int32_t semiring, int32_
         SS_CUDA(cudaEventElapsedTime(&ms, h->ev_a, h->ev_b));
         iter_ms += ms;
         h->iter_ns.push_back((int)(ms * 1.0e6f));
+        // levels run inside one cluster-push launch were timed on the device;
+        // slimsell_get_run_stats takes them from there (marker -1)
+        if (variant == VAR_PUSH_LOCAL)  // (k_before is fresh: adaptive policies read ctl above)
+          for (int extra = h->h_ctl->k - k_before - 1; extra > 0; --extra) h->iter_ns.push_back(-1);
       }
       if (h->h_ctl->done) break;
     }
@@ -946,8 +951,19 @@ ss_status slimsell_get_run_stats(slimsell_handle h, ss_run_stats* out, ss_iter_s
     if (cnt > cap) cnt = cap;
     if (cnt > h->iter_cap) cnt = h->iter_cap;
     SS_CUDA(cudaMemcpy(h_iters, h->iters, sizeof(ss_iter_stats) * (size_t)cnt, cudaMemcpyDeviceToHost));
-    for (int i = 0; i < cnt; ++i)
-      h_iters[i].kernel_ns = (i >= 1 && i - 1 < (int)h->iter_ns.size()) ? h->iter_ns[i - 1] : 0;
+    // host events time each launch; a launch that ran several levels (cluster
+    // push) left -1 markers for its later levels, whose device-side times are
+    // taken from the iteration records and moved out of the launch's first level
+    int owner = -1;
+    for (int i = 0; i < cnt; ++i) {
+      const int host = (i >= 1 && i - 1 < (int)h->iter_ns.size()) ? h->iter_ns[i - 1] : 0;
+      if (host >= 0) {
+        h_iters[i].kernel_ns = host;
+        owner = i;
+      } else {
+        if (owner >= 1) h_iters[owner].kernel_ns = std::max(0, h_iters[owner].kernel_ns - h_iters[i].kernel_ns);
+      }
+    }
   }
   return s;
 }

@@ -400,10 +400,19 @@ __device__ __forceinline__ void local_scatter(const Dev& d, LocalSmem& S, int p0
   }
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 template <int SR, int C>
-__global__ void __launch_bounds__(LOCAL_THREADS, 1) k_push_local(Dev d, IterLaunch il, int max_levels) {
+__global__ void __launch_bounds__(LOCAL_THREADS, 1) k_push_local(Dev d, IterLaunch il, int max_levels,
+                                                                 int time_levels) {
   constexpr int BATCH = (SR == SS_REAL) ? LOCAL_BATCH / 2 : LOCAL_BATCH;  // registers
   LocalSmem& S = *reinterpret_cast<LocalSmem*>(ss_local_smem);
+  // per-level timing (profiling): the first level also carries the launch's entry
+  unsigned long long t_prev = time_levels ? global_ns() : 0ull;
   cg::cluster_group cl = cg::this_cluster();
   const int G = (int)cl.num_blocks();  // 8 or 16
   const int lg = 31 - __clz(G);
@@ -683,6 +692,11 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) k_push_local(Dev d, IterLaun
                     VAR_PUSH_LOCAL, rank == 0);
       S.ctl.list_level = k;
       S.ctl.list_prev_ok = 1;
+      if (time_levels && rank == 0 && k < d.iter_cap) {  // device-side time of this level
+        const unsigned long long t = global_ns();
+        d.iters[k].kernel_ns = (int)min(t - t_prev, 2000000000ull);
+        t_prev = t;
+      }
     }
     reached_deg += td;
     if (rank == 0 && wid == LOCAL_THREADS / 32 - 1 && lane < 7 && k < d.iter_cap) {
@@ -754,6 +768,7 @@ int push_local_cluster_size() {
 template <int SR, int C>
 static ss_status launch_push_local_c(const slimsell_graph* h, const Dev& d, const IterLaunch& il,
                                      int max_levels, cudaStream_t st) {
+  const int time_levels = h->profiling ? 1 : 0;
   static bool configured = false;
   auto kern = k_push_local<SR, C>;
   if (!configured) {
@@ -775,7 +790,7 @@ static ss_status launch_push_local_c(const slimsell_graph* h, const Dev& d, cons
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  SS_CUDA(cudaLaunchKernelEx(&cfg, kern, d, il, max_levels));
+  SS_CUDA(cudaLaunchKernelEx(&cfg, kern, d, il, max_levels, time_levels));
   return SS_OK;
 }
 
