@@ -634,12 +634,10 @@ int vertex_grid(const slimsell_graph* h, int threads) {
 template <int SR, int C, int MODE>
 static ss_status launch_pull(const slimsell_graph* h, const Dev& d, const IterLaunch& il,
                              cudaStream_t st) {
-  static bool configured = false;
-  if (!configured) {
+  static std::atomic<unsigned long long> configured{0};
+  if (first_on_device(configured))
     SS_CUDA(cudaFuncSetAttribute(k_pull<SR, C, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  SS_SMEM_LIMIT_BYTES));
-    configured = true;
-  }
   k_pull<SR, C, MODE><<<pull_grid(h), PULL_THREADS, (size_t)(d.smem_words + SMEM_GUARD) * 4, st>>>(
       d, il.variant, il.cond, il.use_cond);
   SS_CUDA(cudaGetLastError());

@@ -1,6 +1,8 @@
 // Internal definitions shared by the CUDA translation units of libslimsell.
 #pragma once
 
+#include <atomic>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -116,6 +118,17 @@ struct Dev {
   int iter_cap;
 };
 
+}  // namespace ss
+
+namespace ss {
+// True the first time a call site asks on the current device (host code sets
+// per-device kernel attributes once per device; the bit is per call site).
+inline bool first_on_device(std::atomic<unsigned long long>& done) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return true;
+  const unsigned long long bit = 1ull << dev;
+  return !(done.fetch_or(bit) & bit);
+}
 }  // namespace ss
 
 struct slimsell_graph {

@@ -251,8 +251,8 @@ static ss_status launch_multi_cw(const slimsell_graph* h, const MultiDev& m, boo
     set_error("slimsell_bfs_multi: C * ceil(k / 64) must be at least 32");
     return SS_ERR_UNSUPPORTED;
   } else {
-    static int grid[2] = {0, 0};
-    int& g = grid[slimwork ? 1 : 0];
+    static int grid[64][2];  // per device (zero: not measured yet)
+    int& g = grid[h->device & 63][slimwork ? 1 : 0];
     if (!g) {
       int b = 0;
       if (slimwork) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_multi_pull<C, W, true>, C * W, 0);

@@ -769,12 +769,11 @@ template <int SR, int C>
 static ss_status launch_push_local_c(const slimsell_graph* h, const Dev& d, const IterLaunch& il,
                                      int max_levels, cudaStream_t st) {
   const int time_levels = h->profiling ? 1 : 0;
-  static bool configured = false;
+  static std::atomic<unsigned long long> configured{0};
   auto kern = k_push_local<SR, C>;
-  if (!configured) {
+  if (first_on_device(configured)) {
     SS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(LocalSmem)));
     SS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-    configured = true;
   }
   k_push_local_prep<<<vertex_grid(h, 32 * PUSH_THREADS), PUSH_THREADS, 0, st>>>(d);
   SS_CUDA(cudaGetLastError());

@@ -349,11 +349,10 @@ ss_status slimsell_mlp_train_step(float* d_w, float* d_adam_m, float* d_adam_v, 
     return SS_ERR_INVALID;
   }
   const size_t smem = sizeof(float) * (size_t)batch * (F_IN + 4 * F_H + F_OUT);
-  static bool configured = false;
-  if (!configured) {
+  static std::atomic<unsigned long long> configured{0};
+  if (first_on_device(configured)) {
     const size_t maxsm = sizeof(float) * (size_t)TRAIN_MAX_BATCH * (F_IN + 4 * F_H + F_OUT);
     SS_CUDA(cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)maxsm));
-    configured = true;
   }
   k_mlp_train<<<1, TRAIN_THREADS, smem, (cudaStream_t)stream>>>(d_w, d_adam_m, d_adam_v, step, d_x,
                                                                  d_t, d_mask, batch, lr, d_grad,
