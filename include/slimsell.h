@@ -127,7 +127,9 @@ typedef struct {
  *              into ceil(cl / split_w) work items (Section III-D); 0 disables.
  * The call synchronises `stream` (it needs the layout size to allocate col).
  * Errors: SS_ERR_INVALID (n < 1, nnz < 0, bad C, sigma < 1, split_w < 0,
- * NULL pointers), SS_ERR_OOM, SS_ERR_CUDA.  *out is NULL on failure.
+ * NULL pointers), SS_ERR_OOM, SS_ERR_CUDA (also when the device cannot place
+ * the cluster push's thread-block cluster of 8 or 16 CTAs).  *out is NULL on
+ * failure.
  */
 ss_status slimsell_build(const int64_t* d_row_ptr, const int32_t* d_col, int32_t n, int64_t nnz,
                          int32_t C, int32_t sigma, int32_t split_w, void* stream,
