@@ -363,6 +363,19 @@ def batched_learned(ss, torch, g, h, roots, args, stream, dev, runs_edges):
         ms = e0.elapsed_time(e1) / reps
         out[f"multi_{k}"] = edges / (ms / 1000.0) / 1e9
         out[f"multi_{k}_ms"] = ms
+        if k == 64:  # the same sources with largest-id parents as well
+            par = torch.empty((g.n, k), dtype=torch.int32, device=dev)
+            ss.slimsell_bfs_multi_parents(h, r_d, ss.V_SLIMWORK, dist, par, stream)  # warm
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                ss.slimsell_bfs_multi_parents(h, r_d, ss.V_SLIMWORK, dist, par, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            out[f"multi_{k}_parents"] = edges / (ms / 1000.0) / 1e9
+            out[f"multi_{k}_parents_ms"] = ms
+            del par
         del dist
     ss.slimsell_selector_load(h, None)
     out["selector_weights"] = w

@@ -175,6 +175,22 @@ ss_status slimsell_bfs_multi(slimsell_handle h, const int32_t* d_roots, int32_t 
                              int32_t* d_dist, void* stream);
 
 /*
+ * Multi-source BFS with parents (an extension beyond the paper): as
+ * slimsell_bfs_multi, plus
+ *   d_parent int32[n][k] device or NULL: VERTEX-major, d_parent[v * k + s] =
+ *            the largest-id neighbour of v one level closer to roots[s]
+ *            (roots[s] for the root itself, -1 if unreached): for every source,
+ *            the canonical parent that slimsell_bfs returns for that root.
+ * Parents are found by a pass after each level: neighbours are stored in
+ * descending original id, so for each source a vertex gained, the first
+ * neighbour that was in that source's previous frontier is its parent.
+ * slimsell_bfs_multi is this call with d_parent = NULL.
+ * Errors: as slimsell_bfs_multi.
+ */
+ss_status slimsell_bfs_multi_parents(slimsell_handle h, const int32_t* d_roots, int32_t k,
+                                     int32_t policy, int32_t* d_dist, int32_t* d_parent, void* stream);
+
+/*
  * Batched BFS over many graphs (an extension beyond the paper): one executable
  * CUDA graph holding, per handle, the chain init -> root -> device-side
  * iteration loop -> output, so that one launch runs every BFS and the chains

@@ -69,6 +69,7 @@ def lib():
         "slimsell_build": (i32, [_VP, _VP, i32, i64, i32, i32, i32, _VP, ctypes.POINTER(_VP)]),
         "slimsell_bfs": (i32, [_VP, i32, i32, i32, _VP, _VP, _VP]),
         "slimsell_bfs_multi": (i32, [_VP, _VP, i32, i32, _VP, _VP]),
+        "slimsell_bfs_multi_parents": (i32, [_VP, _VP, i32, i32, _VP, _VP, _VP]),
         "slimsell_get_info": (i32, [_VP, ctypes.POINTER(ss_info)]),
         "slimsell_get_run_stats": (i32, [_VP, ctypes.POINTER(ss_run_stats),
                                          ctypes.POINTER(ss_iter_stats), i32]),
@@ -98,7 +99,8 @@ def lib():
 
 
 def exported_symbols() -> list[str]:
-    return ["slimsell_build", "slimsell_bfs", "slimsell_bfs_multi", "slimsell_get_info", "slimsell_get_run_stats",
+    return ["slimsell_build", "slimsell_bfs", "slimsell_bfs_multi", "slimsell_bfs_multi_parents",
+            "slimsell_get_info", "slimsell_get_run_stats",
             "slimsell_set_profiling", "slimsell_set_option", "slimsell_export_layout",
             "slimsell_destroy",
             "slimsell_sigma_sort_noalloc", "slimsell_selector_load", "slimsell_get_features",
@@ -149,6 +151,13 @@ def slimsell_bfs_multi(h: int, roots: torch.Tensor, policy: int, dist: torch.Ten
     _check("slimsell_bfs_multi", lib().slimsell_bfs_multi(
         h, _ptr(roots, torch.int32, "roots"), int(roots.numel()), int(policy),
         _ptr(dist, torch.int32, "dist"), _stream(stream)))
+
+
+def slimsell_bfs_multi_parents(h: int, roots: torch.Tensor, policy: int, dist: torch.Tensor | None,
+                               parent: torch.Tensor | None, stream=None) -> None:
+    _check("slimsell_bfs_multi_parents", lib().slimsell_bfs_multi_parents(
+        h, _ptr(roots, torch.int32, "roots"), int(roots.numel()), int(policy),
+        _ptr(dist, torch.int32, "dist"), _ptr(parent, torch.int32, "parent"), _stream(stream)))
 
 
 def slimsell_get_info(h: int) -> ss_info:
@@ -322,6 +331,20 @@ class SlimSellGraph:
             dist = torch.empty((self.n, r.numel()), dtype=torch.int32, device=dev)
         slimsell_bfs_multi(self.h, r, pol, dist, stream)
         return dist
+
+    def bfs_multi_parents(self, roots, policy="slimwork", dist=None, parent=None,
+                          want_dist: bool = True, stream=None):
+        """k-source BFS with largest-id parents; returns (dist, parent), both (n, k)
+        int32 tensors (vertex-major; dist None when want_dist is False)."""
+        pol = POLICIES[policy] if isinstance(policy, str) else int(policy)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        r = torch.as_tensor(roots, dtype=torch.int32).to(dev)
+        if dist is None and want_dist:
+            dist = torch.empty((self.n, r.numel()), dtype=torch.int32, device=dev)
+        if parent is None:
+            parent = torch.empty((self.n, r.numel()), dtype=torch.int32, device=dev)
+        slimsell_bfs_multi_parents(self.h, r, pol, dist, parent, stream)
+        return dist, parent
 
     def run_stats(self, cap: int = 0):
         return slimsell_get_run_stats(self.h, cap)

@@ -18,6 +18,13 @@
 // frontier (bit u set iff some source has u in its frontier, kept in the
 // single-source frontier bitmaps fb[], unused here) is tested first, and a
 // thread whose 64 sources have all visited its row gathers nothing.
+//
+// Parents (optional) come from a separate pass after each level: a row's
+// neighbours are stored in descending original id, so for each source that
+// the row gained at level k, the first neighbour in storage order that was in
+// that source's level-(k-1) frontier is its largest-id parent.  The pass
+// reads F[(k-1)&1] and the summary bitmap of level k-1, both still intact
+// until level k+1 overwrites them.
 #include <algorithm>
 #include <cstdint>
 #include <vector>
@@ -213,7 +220,7 @@ __global__ void k_multi_init(MultiDev m, int W) {
   }
 }
 
-__global__ void k_multi_roots(MultiDev m, int W) {
+__global__ void k_multi_roots(MultiDev m, int W, int* parent) {
   const Dev& d = m.d;
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < m.k; s += gridDim.x * blockDim.x) {
     const int v = m.roots[s];
@@ -223,6 +230,7 @@ __global__ void k_multi_roots(MultiDev m, int W) {
     atomicOr(m.F[0] + r * W + s / 64, bit);
     atomicOr(d.fb[0] + (r >> 5), 1u << (r & 31));
     if (m.dist) m.dist[(long long)v * m.k + s] = 0;
+    if (parent) parent[(long long)v * m.k + s] = v;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     Ctl* c = d.ctl;
@@ -241,6 +249,92 @@ __global__ void k_multi_roots(MultiDev m, int W) {
     st.frontier = m.k; st.frontier_degree = (long long)rd; st.slots = 0; st.active_chunks = 0;
     st.variant = -1; st.kernel_ns = 0;
     d.iters[0] = st;
+  }
+}
+
+// Parents of the sources each row gained at `level`: (row, w) walks the row's
+// neighbours in storage order (descending original id) and gives each new
+// source of word w the first neighbour found in its frontier of level-1,
+// stopping once every new source has one.  Each lane first walks its own row
+// for up to MULTI_PAR_SHORT neighbours; rows still unresolved then are walked
+// by the whole warp, 32 neighbours per step, the candidates taken in lane
+// (= storage) order.  Plain stores: one lane owns each (row, word) entry.
+constexpr int MULTI_PAR_SHORT = 32;
+
+__global__ void __launch_bounds__(256) k_multi_parents(MultiDev m, int W, int lgW, int level, int* parent) {
+  const Dev& d = m.d;
+  const unsigned long long* Fp = m.F[(level - 1) & 1];
+  const unsigned long long* Fn = m.F[level & 1];
+  const unsigned* FAp = d.fb[(level - 1) & 1];
+  const long long words = (long long)d.n_pad << lgW;
+  const int lane = threadIdx.x & 31;
+  const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long i0 = warp0 * 32; i0 < words; i0 += nwarps * 32) {
+    const long long i = i0 + lane;
+    unsigned long long rem = i < words ? Fn[i] : 0ull;
+    const long long row = i >> lgW;
+    const int w = (int)(i & (W - 1));
+    const int v = rem ? d.perm[row] : -1;
+    if (v < 0) rem = 0ull;  // padding rows never gain a source
+    long long base = 0;
+    int len = 0, j = 0;
+    int* prow = nullptr;
+    if (rem) {
+      prow = parent + (long long)v * m.k + 64 * w;
+      const long long chunk = row / d.C;
+      base = d.cs[chunk] + (row - chunk * d.C);
+      len = d.rdeg[row];  // the row's neighbours come first, padding after
+      for (; j < len && j < MULTI_PAR_SHORT && rem; ++j) {
+        const int u = __ldg(d.col + base + (long long)j * d.C);
+        if (!((__ldg(FAp + (u >> 5)) >> (u & 31)) & 1u)) continue;
+        unsigned long long f = __ldg(Fp + ((long long)u << lgW) + w) & rem;
+        if (!f) continue;
+        rem &= ~f;
+        const int pu = __ldg(d.perm + u);
+        while (f) {
+          prow[__ffsll((long long)f) - 1] = pu;
+          f &= f - 1;
+        }
+      }
+    }
+    unsigned pend = __ballot_sync(SS_FULL_MASK, rem != 0ull);
+    while (pend) {  // long rows, one at a time, by the whole warp
+      const int l = __ffs(pend) - 1;
+      pend &= pend - 1;
+      unsigned long long rl = __shfl_sync(SS_FULL_MASK, rem, l);
+      const long long bl = __shfl_sync(SS_FULL_MASK, base, l);
+      const int nl = __shfl_sync(SS_FULL_MASK, len, l);
+      const int jl = __shfl_sync(SS_FULL_MASK, j, l);
+      const int wl = __shfl_sync(SS_FULL_MASK, w, l);
+      int* const pl = reinterpret_cast<int*>(
+          __shfl_sync(SS_FULL_MASK, reinterpret_cast<unsigned long long>(prow), l));
+      for (int jj = jl; jj < nl && rl; jj += 32) {
+        const int jx = jj + lane;
+        unsigned long long f = 0ull;
+        int u = 0;
+        if (jx < nl) {
+          u = __ldg(d.col + bl + (long long)jx * d.C);
+          if ((__ldg(FAp + (u >> 5)) >> (u & 31)) & 1u) f = __ldg(Fp + ((long long)u << lgW) + wl) & rl;
+        }
+        unsigned cand = __ballot_sync(SS_FULL_MASK, f != 0ull);
+        const int pu = f ? __ldg(d.perm + u) : -1;
+        while (cand) {  // lane order is storage order
+          const int c2 = __ffs(cand) - 1;
+          cand &= cand - 1;
+          const unsigned long long fc = __shfl_sync(SS_FULL_MASK, f, c2) & rl;
+          if (!fc) continue;
+          rl &= ~fc;
+          if (lane == c2) {
+            unsigned long long b = fc;
+            while (b) {
+              pl[__ffsll((long long)b) - 1] = pu;
+              b &= b - 1;
+            }
+          }
+        }
+      }
+    }
   }
 }
 
@@ -314,6 +408,12 @@ static ss_status ensure_multi_scratch(slimsell_graph* h, int W) {
 
 extern "C" ss_status slimsell_bfs_multi(slimsell_handle h, const int32_t* d_roots, int32_t k,
                                         int32_t policy, int32_t* d_dist, void* stream) {
+  return slimsell_bfs_multi_parents(h, d_roots, k, policy, d_dist, nullptr, stream);
+}
+
+extern "C" ss_status slimsell_bfs_multi_parents(slimsell_handle h, const int32_t* d_roots, int32_t k,
+                                                int32_t policy, int32_t* d_dist, int32_t* d_parent,
+                                                void* stream) {
   using namespace ss;
   set_error("");
   if (!h || !d_roots) {
@@ -361,8 +461,11 @@ extern "C" ss_status slimsell_bfs_multi(slimsell_handle h, const int32_t* d_root
   double iter_ms = 0.0;
   if (prof) SS_CUDA(cudaEventRecord(h->ev_c, st));
   if (d_dist) SS_CUDA(cudaMemsetAsync(d_dist, 0xff, sizeof(int) * (size_t)h->n * (size_t)k, st));
+  if (d_parent) SS_CUDA(cudaMemsetAsync(d_parent, 0xff, sizeof(int) * (size_t)h->n * (size_t)k, st));
   k_multi_init<<<8 * h->num_sms, 256, 0, st>>>(m, W);
-  k_multi_roots<<<(k + 255) / 256, 256, 0, st>>>(m, W);
+  k_multi_roots<<<(k + 255) / 256, 256, 0, st>>>(m, W, d_parent);
+  int lgW = 0;
+  while ((1 << lgW) < W) ++lgW;
   SS_CUDA(cudaGetLastError());
   const IterLaunch il{policy, 0, 0};
   const long long max_iter = (long long)h->n + 2;
@@ -374,6 +477,10 @@ extern "C" ss_status slimsell_bfs_multi(slimsell_handle h, const int32_t* d_root
     if (prof) SS_CUDA(cudaEventRecord(h->ev_a, st));
     s = launch_multi(h, m, W, policy == SS_V_SLIMWORK, il, st);
     if (s != SS_OK) return s;
+    if (d_parent) {  // parents of the sources gained at this level
+      k_multi_parents<<<8 * h->num_sms, 256, 0, st>>>(m, W, lgW, (int)(it + 1), d_parent);
+      SS_CUDA(cudaGetLastError());
+    }
     if (prof) SS_CUDA(cudaEventRecord(h->ev_b, st));
     SS_CUDA(cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
     SS_CUDA(cudaStreamSynchronize(st));

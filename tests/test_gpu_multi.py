@@ -102,3 +102,77 @@ def test_distance_writes_aligned_and_not(offset):
     rest = torch.cat([buf[:offset], buf[offset + g.n * 100:]]).cpu().numpy()
     assert (rest == 7).all()  # nothing written outside the output
     G.close()
+
+
+def check_parents(G, g, roots, policy):
+    dist, parent = G.bfs_multi_parents(roots, policy)
+    torch.cuda.synchronize()
+    want = oracle.bfs_multi(g.row_ptr, g.col, roots)  # (k, n)
+    np.testing.assert_array_equal(dist.cpu().numpy(), want.T)
+    got = parent.cpu().numpy()
+    for s, r in enumerate(roots):
+        np.testing.assert_array_equal(got[:, s], oracle.dp(g.row_ptr, g.col, want[s], int(r)),
+                                      err_msg=f"source {s} root {r}")
+
+
+@pytest.mark.parametrize("k", [64, 100, 1024])
+def test_multi_parents_kron(k):
+    """Parents per source equal the oracle's largest-id DP parents, with and without
+    SlimChunk splits (split items combine their candidates with atomicMax)."""
+    g = gg.kronecker(12, seed=9)
+    rng = np.random.default_rng(k)
+    roots = gg.roots(g, min(k, 600), seed=3)
+    roots = np.concatenate([roots, rng.choice(roots, k - len(roots))]) if k > len(roots) else roots
+    for C, w, policy in [(32, 0, "slimwork"), (32, 16, "slimwork"), (64, 64, "full")]:
+        G = ss.SlimSellGraph.from_host(g.row_ptr, g.col, C=C, sigma=g.n, split_w=w)
+        check_parents(G, g, roots.astype(np.int32), policy)
+        G.close()
+
+
+def test_multi_parents_lattice_and_ragged():
+    g = gg.lattice(45, 0.08, seed=2)  # several components: unreached parents stay -1
+    roots = np.array(list(gg.roots(g, 40, seed=4)) + [0, g.n - 1, 7, 7], dtype=np.int32)
+    G = ss.SlimSellGraph.from_host(g.row_ptr, g.col, C=16, sigma=g.n, split_w=2)
+    check_parents(G, g, roots, "slimwork")
+    G.close()
+
+
+def test_multi_parents_without_distances_and_plain_call_unchanged():
+    """dist = NULL with parents; then the parent-less call on the same handle."""
+    g = gg.erdos_renyi(3000, 5.0, seed=7)
+    roots = gg.roots(g, 70, seed=2)
+    G = ss.SlimSellGraph.from_host(g.row_ptr, g.col, C=8, sigma=64, split_w=4)
+    _, parent = G.bfs_multi_parents(roots, "slimwork", want_dist=False)
+    torch.cuda.synchronize()
+    want = oracle.bfs_multi(g.row_ptr, g.col, roots)
+    got = parent.cpu().numpy()
+    for s, r in enumerate(roots):
+        np.testing.assert_array_equal(got[:, s], oracle.dp(g.row_ptr, g.col, want[s], int(r)))
+    check(G, g, roots, "slimwork")
+    G.close()
+
+
+def test_kron22_multi_parents_sampled():
+    """Full-size Kronecker scale 22, 64 sources with parents; 3 sampled sources exact."""
+    g = gg.kronecker(22, seed=1)
+    G = ss.SlimSellGraph.from_host(g.row_ptr, g.col, C=32, sigma=g.n, split_w=256)
+    roots = gg.roots(g, 64, seed=2)
+    dist, parent = G.bfs_multi_parents(roots, "slimwork")
+    torch.cuda.synchronize()
+    for s in (0, 31, 63):
+        d = oracle.bfs_queue(g.row_ptr, g.col, int(roots[s]))
+        np.testing.assert_array_equal(dist[:, s].cpu().numpy(), d)
+        np.testing.assert_array_equal(parent[:, s].cpu().numpy(), oracle.dp(g.row_ptr, g.col, d, int(roots[s])))
+    G.close()
+
+
+def test_multi_parents_far_in_a_long_row():
+    """A row of 1,200 neighbours whose only frontier neighbour at its level is
+    stored last (the smallest id): the walk has to reach the end of the row."""
+    hub = 1300
+    edges = [(u, hub) for u in range(1200)] + [(1200 + t, t) for t in range(100)]
+    g = gg.from_edges(hub + 1, edges, name="far-parent")
+    roots = np.arange(1200, 1270, dtype=np.int32)  # each reaches the hub through one leaf
+    G = ss.SlimSellGraph.from_host(g.row_ptr, g.col, C=32, sigma=g.n, split_w=0)
+    check_parents(G, g, roots, "slimwork")
+    G.close()
