@@ -508,6 +508,53 @@ def roofline_at_scale(ss, torch, scale, nroots, split_w, stream, dev):
     return out
 
 
+def format_ab(ss, torch, g, sigmas, stream, dev, nroots=4):
+    """Speedup of SlimSell over Sell-C-sigma (Section IV): the plain value-vector
+    BFS-SpMV in both formats on the same layout (C = 32, SlimChunk w = 256), for
+    each sigma and semiring; summed device time of the iteration kernels over
+    `nroots` roots, each format warmed up once (which builds the Sell arrays)."""
+    roots = gg.roots(g, nroots, seed=5)
+    rp_d = torch.from_numpy(g.row_ptr).to(dev)
+    col_d = torch.from_numpy(g.col).to(dev)
+    dist = torch.empty(g.n, dtype=torch.int32, device=dev)
+    out = {"n": g.n, "nnz": g.nnz, "roots": nroots}
+    for sigma in sigmas:
+        h = ss.slimsell_build(rp_d, col_d, g.n, g.nnz, 32, sigma, 256, stream)
+        inf = ss.slimsell_get_info(h)
+        edges = 0
+        for r in roots:
+            ss.slimsell_bfs(h, int(r), SR_ID["tropical"], ss.V_SLIMWORK, None, None, stream)
+            st, _ = ss.slimsell_get_run_stats(h)
+            edges += st.reached_degree // 2
+        row = {"sigma": inf.sigma, "slots": inf.slots, "slots_per_nnz": inf.slots / max(1, g.nnz)}
+        for sr in SEMIRINGS:
+            ms = {}
+            for name, f in (("slimsell", ss.FORMAT_SLIMSELL), ("sell", ss.FORMAT_SELL)):
+                ss.slimsell_bfs_spmv(h, int(roots[0]), SR_ID[sr], f, dist, stream, timed=True)
+                ms[name] = sum(ss.slimsell_bfs_spmv(h, int(r), SR_ID[sr], f, dist, stream, timed=True)
+                               for r in roots)
+            row[sr] = {"slimsell_ms": ms["slimsell"], "sell_ms": ms["sell"],
+                       "speedup_slimsell_over_sell": ms["sell"] / ms["slimsell"],
+                       "gteps_slimsell": edges / (ms["slimsell"] / 1000.0) / 1e9,
+                       "gteps_sell": edges / (ms["sell"] / 1000.0) / 1e9}
+        out[f"sigma_{inf.sigma}"] = row
+        ss.slimsell_destroy(h)
+        torch.cuda.empty_cache()
+    del rp_d, col_d, dist
+    return out
+
+
+def format_ab_sections(ss, torch, stream, dev, g22=None):
+    """The format comparison on Kronecker 22 with sigma = C = 32 (the paper's
+    sigma = 2^4 rounded up to a multiple of C) and on Kronecker 24 (the paper's
+    n = 2^24) with sigma = 2^12 and 2^18; at scale 24 sigma = 32 would need about
+    20 slots per edge (over 150 GB with the Sell arrays)."""
+    g22 = g22 if g22 is not None else gg.kronecker(22, seed=1)
+    out = {"kronecker22": format_ab(ss, torch, g22, (32,), stream, dev)}
+    out["kronecker24"] = format_ab(ss, torch, gg.kronecker(24, seed=1), (1 << 12, 1 << 18), stream, dev)
+    return out
+
+
 def selector_heldout(ss, torch, stream, dev, weights):
     """The selector trained above, on graphs it never saw: Kronecker scale 25
     (edgefactor 16) and a 8192 x 8192 lattice with 5% of its edges deleted;
@@ -610,9 +657,10 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-scale24", action="store_true")
     ap.add_argument("--no-high-diameter", action="store_true")
+    ap.add_argument("--no-format-ab", action="store_true")
     ap.add_argument("--ref-seconds", type=float, default=None,
                     help="reference arm: seconds of oracle work per step (default 10-30)")
-    ap.add_argument("--only", choices=["high-diameter"], default=None,
+    ap.add_argument("--only", choices=["high-diameter", "format-ab"], default=None,
                     help="run one section alone and print it (profiling runs)")
     ap.add_argument("--host-loop", action="store_true",
                     help="host-driven iteration loop (kernels visible to a profiler)")
@@ -636,6 +684,10 @@ def main():
         if rank == 0:
             print(json.dumps({"high_diameter": high_diameter(ss, torch, stream, dev, None, nroots=args.roots,
                                                              host_loop=args.host_loop)}), flush=True)
+        return
+    if args.only == "format-ab":
+        if rank == 0:
+            print(json.dumps({"format_ab": format_ab_sections(ss, torch, stream, dev)}), flush=True)
         return
 
     g = gg.kronecker(args.scale, seed=1)
@@ -775,6 +827,9 @@ def main():
     if not args.no_scale24 and rank == 0:
         torch.cuda.empty_cache()
         line["scale24"] = roofline_at_scale(ss, torch, 24, 8, args.split_w, stream, dev)
+    if not args.no_format_ab and rank == 0:
+        torch.cuda.empty_cache()
+        line["format_ab"] = format_ab_sections(ss, torch, stream, dev, g)
     if not args.no_high_diameter and rank == 0:
         torch.cuda.empty_cache()
         line["high_diameter"] = high_diameter(ss, torch, stream, dev, sel_w)

@@ -60,17 +60,19 @@ typedef enum {
   SS_V_SLIMWORK = 1,      /* skip chunks whose rows are all visited (SlimWork, Section III-C) */
   SS_V_PUSH = 2,          /* compacted-frontier push (work-avoidance variant, Section V); falls
                              back to PULL_FILTERED when the frontier exceeds the unit buffer;
-                             frontiers of at most 8192 vertices and 65536 edges run in the
-                             single-block push (SS_VARIANT_PUSH_LOCAL)                          */
+                             frontiers of at most 4096 vertices and 8192 edges per CTA of a
+                             thread-block cluster run in the cluster push
+                             (SS_VARIANT_PUSH_LOCAL)                                           */
   SS_V_PULL_FILTERED = 3, /* pull over unvisited rows only, stopping at the first hit         */
   SS_V_HEURISTIC = 4,     /* per-iteration choice by a frontier-size rule                      */
   SS_V_LEARNED = 5        /* per-iteration choice by the loaded selector MLP                   */
 } ss_policy;
 
-/* Executed-variant id (ss_iter_stats.variant, not a policy) of the single-block
- * push: one 1024-thread block runs consecutive small levels in one launch with
- * the frontier kept as a vertex list; push and the adaptive policies use it for
- * frontiers of at most 8192 vertices and 65536 edges (high-diameter graphs). */
+/* Executed-variant id (ss_iter_stats.variant, not a policy) of the cluster
+ * push: one thread-block cluster (16 CTAs of 1024 threads, else 8) runs
+ * consecutive small levels in one launch with the frontier kept as vertex
+ * lists in shared memory; push and the adaptive policies use it for frontiers
+ * of at most 4096 vertices and 8192 edges per CTA (high-diameter graphs). */
 #define SS_VARIANT_PUSH_LOCAL 4
 
 /* Layout summary of a built handle. */
@@ -189,6 +191,37 @@ ss_status slimsell_bfs_multi(slimsell_handle h, const int32_t* d_roots, int32_t 
  */
 ss_status slimsell_bfs_multi_parents(slimsell_handle h, const int32_t* d_roots, int32_t k,
                                      int32_t policy, int32_t* d_dist, int32_t* d_parent, void* stream);
+
+/* Storage formats of slimsell_bfs_spmv. */
+typedef enum {
+  SS_FORMAT_SLIMSELL = 0, /* value inferred from col (-1 = padding, skipped), Section III-B */
+  SS_FORMAT_SELL = 1      /* Sell-C-sigma: explicit val array, padding col 0 with the
+                             semiring's zero as its value, Section II-D                    */
+} ss_format;
+
+/*
+ * Storage-format comparison (Section IV, the speedup of SlimSell over
+ * Sell-C-sigma): single-source BFS as the plain value-vector BFS-SpMV of
+ * Section III-A (fp32 value vectors; every iteration streams every slot of the
+ * handle's layout, SlimChunk items combined with atomics; no SlimWork, no
+ * bitmaps), in either format.  The two formats differ only in where a slot's
+ * matrix value comes from; results are identical.
+ *   root      vertex id in [0, n)
+ *   semiring  ss_semiring
+ *   format    ss_format; SS_FORMAT_SELL builds the Sell-C-sigma arrays (col with
+ *             padding 0, and one val array per value encoding: 1/inf for the
+ *             tropical semiring, 1/0 for the others; 12 bytes per slot) from the
+ *             handle's layout on first use and keeps them until
+ *             slimsell_destroy.
+ *   d_dist    int32[n] device, required: BFS distances (-1 unreached).
+ *   kernel_ms host double* or NULL: if given, the summed device time of the
+ *             iterations' kernels (CUDA events around each level's two launches).
+ * Synchronous with respect to the host (the loop reads a counter per level).
+ * Errors: SS_ERR_INVALID (NULL, root or semiring out of range, unknown format),
+ *         SS_ERR_OOM, SS_ERR_CUDA.
+ */
+ss_status slimsell_bfs_spmv(slimsell_handle h, int32_t root, int32_t semiring, int32_t format,
+                            int32_t* d_dist, double* kernel_ms, void* stream);
 
 /*
  * Batched BFS over many graphs (an extension beyond the paper): one executable

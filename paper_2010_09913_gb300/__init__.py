@@ -18,7 +18,9 @@ from .build import LIB, build  # noqa: F401  (build() compiles the library)
 TROPICAL, REAL, BOOLEAN, SELMAX = 0, 1, 2, 3
 SEMIRINGS = {"tropical": TROPICAL, "real": REAL, "boolean": BOOLEAN, "selmax": SELMAX}
 V_FULL, V_SLIMWORK, V_PUSH, V_PULL_FILTERED, V_HEURISTIC, V_LEARNED = range(6)
-VARIANT_PUSH_LOCAL = 4  # executed-variant id of the single-block push (iteration stats only)
+VARIANT_PUSH_LOCAL = 4  # executed-variant id of the cluster push (iteration stats only)
+FORMAT_SLIMSELL, FORMAT_SELL = 0, 1  # storage formats of slimsell_bfs_spmv
+FORMATS = {"slimsell": FORMAT_SLIMSELL, "sell": FORMAT_SELL}
 POLICIES = {"full": V_FULL, "slimwork": V_SLIMWORK, "push": V_PUSH,
             "pull_filtered": V_PULL_FILTERED, "heuristic": V_HEURISTIC, "learned": V_LEARNED}
 STATUS = {0: "SS_OK", 1: "SS_ERR_INVALID", 2: "SS_ERR_OOM", 3: "SS_ERR_CUDA",
@@ -70,6 +72,7 @@ def lib():
         "slimsell_bfs": (i32, [_VP, i32, i32, i32, _VP, _VP, _VP]),
         "slimsell_bfs_multi": (i32, [_VP, _VP, i32, i32, _VP, _VP]),
         "slimsell_bfs_multi_parents": (i32, [_VP, _VP, i32, i32, _VP, _VP, _VP]),
+        "slimsell_bfs_spmv": (i32, [_VP, i32, i32, i32, _VP, ctypes.POINTER(ctypes.c_double), _VP]),
         "slimsell_get_info": (i32, [_VP, ctypes.POINTER(ss_info)]),
         "slimsell_get_run_stats": (i32, [_VP, ctypes.POINTER(ss_run_stats),
                                          ctypes.POINTER(ss_iter_stats), i32]),
@@ -100,6 +103,7 @@ def lib():
 
 def exported_symbols() -> list[str]:
     return ["slimsell_build", "slimsell_bfs", "slimsell_bfs_multi", "slimsell_bfs_multi_parents",
+            "slimsell_bfs_spmv",
             "slimsell_get_info", "slimsell_get_run_stats",
             "slimsell_set_profiling", "slimsell_set_option", "slimsell_export_layout",
             "slimsell_destroy",
@@ -158,6 +162,17 @@ def slimsell_bfs_multi_parents(h: int, roots: torch.Tensor, policy: int, dist: t
     _check("slimsell_bfs_multi_parents", lib().slimsell_bfs_multi_parents(
         h, _ptr(roots, torch.int32, "roots"), int(roots.numel()), int(policy),
         _ptr(dist, torch.int32, "dist"), _ptr(parent, torch.int32, "parent"), _stream(stream)))
+
+
+def slimsell_bfs_spmv(h: int, root: int, semiring: int, fmt: int, dist: torch.Tensor,
+                      stream=None, timed: bool = False):
+    """Value-vector BFS-SpMV in the SlimSell or Sell-C-sigma format; returns the
+    summed device time of its kernels in ms when timed, else None."""
+    ms = ctypes.c_double(0.0)
+    _check("slimsell_bfs_spmv", lib().slimsell_bfs_spmv(
+        h, int(root), int(semiring), int(fmt), _ptr(dist, torch.int32, "dist"),
+        ctypes.byref(ms) if timed else None, _stream(stream)))
+    return ms.value if timed else None
 
 
 def slimsell_get_info(h: int) -> ss_info:
@@ -330,6 +345,15 @@ class SlimSellGraph:
         if dist is None and want_dist:
             dist = torch.empty((self.n, r.numel()), dtype=torch.int32, device=dev)
         slimsell_bfs_multi(self.h, r, pol, dist, stream)
+        return dist
+
+    def bfs_spmv(self, root: int, semiring="tropical", fmt="slimsell", dist=None, stream=None):
+        """Plain value-vector BFS-SpMV in either storage format; returns dist."""
+        sr = SEMIRINGS[semiring] if isinstance(semiring, str) else int(semiring)
+        f = FORMATS[fmt] if isinstance(fmt, str) else int(fmt)
+        if dist is None:
+            dist = torch.empty(self.n, dtype=torch.int32, device=torch.device("cuda", torch.cuda.current_device()))
+        slimsell_bfs_spmv(self.h, root, sr, f, dist, stream)
         return dist
 
     def bfs_multi_parents(self, roots, policy="slimwork", dist=None, parent=None,
