@@ -9,6 +9,8 @@ shares no code with it; it exists to say what the right answer is.
 * ``bfs_semiring``   algebraic BFS over the tropical, real, boolean and sel-max
                      semirings on the plain CSR (Section III-A), dense vectors.
 * ``bfs_multi``      k independent queue BFS runs (multi-source extension).
+* ``bc``             betweenness centrality over a set of sources (Brandes'
+                     dependency accumulation; the paper's future-work algorithms).
 * ``slimsell_layout`` Sell-C-sigma / SlimSell layout (Sections II-D and III-B):
                      sigma-window degree sort, chunk tables cs/cl, column-major
                      col with -1 padding, SlimChunk split table (Section III-D).
@@ -62,6 +64,8 @@ def _load():
                                         i32p, i32p, f64p, i64p, ctypes.c_int32]
     lib.oracle_bfs_multi.restype = ctypes.c_int64
     lib.oracle_bfs_multi.argtypes = [ctypes.c_int32, i64p, i32p, i32p, ctypes.c_int32, i32p]
+    lib.oracle_bc.restype = ctypes.c_int32
+    lib.oracle_bc.argtypes = [ctypes.c_int32, i64p, i32p, i32p, ctypes.c_int32, f64p]
     _lib = lib
     return lib
 
@@ -152,6 +156,21 @@ def reached_edges(row_ptr, dist) -> int:
     """
     deg = np.diff(np.asarray(row_ptr, dtype=np.int64))
     return int(deg[np.asarray(dist) >= 0].sum() // 2)
+
+
+def bc(row_ptr, col, sources) -> np.ndarray:
+    """Betweenness centrality summed over ``sources`` (fp64, Brandes):
+    bc[v] = sum over s in sources, t != s, v of sigma_st(v) / sigma_st."""
+    lib = _load()
+    row_ptr, col = _csr(row_ptr, col)
+    n = row_ptr.shape[0] - 1
+    src = np.ascontiguousarray(sources, dtype=np.int32)
+    out = np.empty(max(n, 1), dtype=np.float64)
+    r = lib.oracle_bc(n, _p(row_ptr, ctypes.c_int64), _p(col, ctypes.c_int32), _p(src, ctypes.c_int32),
+                      int(src.shape[0]), _p(out, ctypes.c_double))
+    if r != 0:
+        raise ValueError("oracle_bc: bad source")
+    return out[:n]
 
 
 def slimsell_layout(row_ptr, col, C: int, sigma: int, split_w: int = 0):

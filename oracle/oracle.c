@@ -20,6 +20,14 @@
  *                                  f_k = nn(x_k) - g_k, p_k = p_{k-1} + not(p_{k-1}) (.) x_k,
  *                                  then x_k = nn(x_k) (.) (1..n)
  *   oracle_bfs_multi     k independent queue BFS runs (multi-source extension).
+ *   oracle_bc            betweenness centrality summed over a set of sources, by
+ *                        Brandes' dependency accumulation (the "other algorithms"
+ *                        the paper names as future work in its conclusion): for each
+ *                        source s, a queue BFS counts shortest paths sigma_s, then
+ *                        in reverse BFS order
+ *                        delta_s(v) = sum over neighbours w with d(w) = d(v) + 1 of
+ *                                     sigma_s(v) / sigma_s(w) * (1 + delta_s(w)),
+ *                        and bc(v) += delta_s(v) for v != s.
  *
  * Floating point values (tropical distances, real-semiring path counts) are
  * fp64.  Parity status: every function here is pinned by the CPU tests
@@ -213,4 +221,45 @@ int64_t oracle_bfs_multi(int32_t n, const int64_t* row_ptr, const int32_t* col,
     total += r;
   }
   return total;
+}
+
+/* Betweenness centrality over the given sources (Brandes): bc[v] = sum over
+ * sources s and targets t != s, v of sigma_st(v) / sigma_st.  On an undirected
+ * graph with every vertex as a source each unordered pair counts twice.
+ * Returns 0, or -1 on a bad source. */
+int32_t oracle_bc(int32_t n, const int64_t* row_ptr, const int32_t* col, const int32_t* sources,
+                  int32_t k, double* bc) {
+  int32_t* dist = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  int32_t* order = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  double* sigma = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double* delta = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  for (int32_t v = 0; v < n; ++v) bc[v] = 0.0;
+  int32_t status = 0;
+  for (int32_t q = 0; q < k; ++q) {
+    const int32_t s = sources[q];
+    if (s < 0 || s >= n) { status = -1; break; }
+    for (int32_t v = 0; v < n; ++v) { dist[v] = -1; sigma[v] = 0.0; delta[v] = 0.0; }
+    /* forward: BFS order and shortest-path counts */
+    int32_t head = 0, tail = 0;
+    dist[s] = 0; sigma[s] = 1.0; order[tail++] = s;
+    while (head < tail) {
+      const int32_t v = order[head++];
+      for (int64_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+        const int32_t w = col[e];
+        if (dist[w] < 0) { dist[w] = dist[v] + 1; order[tail++] = w; }
+        if (dist[w] == dist[v] + 1) sigma[w] += sigma[v];
+      }
+    }
+    /* backward: dependencies in reverse BFS order */
+    for (int32_t i = tail - 1; i >= 0; --i) {
+      const int32_t v = order[i];
+      for (int64_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+        const int32_t w = col[e];
+        if (dist[w] == dist[v] + 1) delta[v] += sigma[v] / sigma[w] * (1.0 + delta[w]);
+      }
+      if (v != s) bc[v] += delta[v];
+    }
+  }
+  free(dist); free(order); free(sigma); free(delta);
+  return status;
 }
