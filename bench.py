@@ -544,6 +544,20 @@ def format_ab(ss, torch, g, sigmas, stream, dev, nroots=4):
     return out
 
 
+def bc_measure(ss, torch, g, h, stream, dev, nsources=8):
+    """Betweenness centrality (Brandes, fp64) over `nsources` seeded sources on
+    the benchmark graph's handle: summed device time of the level kernels and
+    TEPS = sources * undirected edges / time."""
+    src = torch.from_numpy(gg.roots(g, nsources, seed=11)).to(dev)
+    out = torch.empty(g.n, dtype=torch.float64, device=dev)
+    ss.slimsell_bc(h, src[:1], out, stream)  # warm-up (allocates the scratch)
+    ms = ss.slimsell_bc(h, src, out, stream, timed=True)
+    m = g.nnz // 2
+    return {"sources": nsources, "kernel_ms": ms, "ms_per_source": ms / nsources,
+            "gteps": nsources * m / (ms / 1000.0) / 1e9,
+            "definition": "sources x undirected edges / summed device time of the level kernels"}
+
+
 def format_ab_sections(ss, torch, stream, dev, g22=None):
     """The format comparison on Kronecker 22 with sigma = C = 32 (the paper's
     sigma = 2^4 rounded up to a multiple of C) and on Kronecker 24 (the paper's
@@ -658,9 +672,10 @@ def main():
     ap.add_argument("--no-scale24", action="store_true")
     ap.add_argument("--no-high-diameter", action="store_true")
     ap.add_argument("--no-format-ab", action="store_true")
+    ap.add_argument("--no-bc", action="store_true")
     ap.add_argument("--ref-seconds", type=float, default=None,
                     help="reference arm: seconds of oracle work per step (default 10-30)")
-    ap.add_argument("--only", choices=["high-diameter", "format-ab"], default=None,
+    ap.add_argument("--only", choices=["high-diameter", "format-ab", "bc"], default=None,
                     help="run one section alone and print it (profiling runs)")
     ap.add_argument("--host-loop", action="store_true",
                     help="host-driven iteration loop (kernels visible to a profiler)")
@@ -684,6 +699,15 @@ def main():
         if rank == 0:
             print(json.dumps({"high_diameter": high_diameter(ss, torch, stream, dev, None, nroots=args.roots,
                                                              host_loop=args.host_loop)}), flush=True)
+        return
+    if args.only == "bc":
+        if rank == 0:
+            g = gg.kronecker(args.scale, seed=1)
+            rp_d = torch.from_numpy(g.row_ptr).to(dev)
+            col_d = torch.from_numpy(g.col).to(dev)
+            h = ss.slimsell_build(rp_d, col_d, g.n, g.nnz, 32, g.n, args.split_w, stream)
+            print(json.dumps({"bc": bc_measure(ss, torch, g, h, stream, dev)}), flush=True)
+            ss.slimsell_destroy(h)
         return
     if args.only == "format-ab":
         if rank == 0:
@@ -822,6 +846,8 @@ def main():
         line["e2e"] = e2e_measure(ss, torch, g, roots, args, stream, dev, pg)
     if not args.no_ablations and rank == 0:
         line["ablations"] = ablations(ss, torch, g, roots[:8], h, rp_d, col_d, args, stream, dev)
+    if not args.no_bc and rank == 0:
+        line["bc"] = bc_measure(ss, torch, g, h, stream, dev)
     ss.slimsell_destroy(h)
     del rp_d, col_d
     if not args.no_scale24 and rank == 0:

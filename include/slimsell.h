@@ -224,6 +224,31 @@ ss_status slimsell_bfs_spmv(slimsell_handle h, int32_t root, int32_t semiring, i
                             int32_t* d_dist, double* kernel_ms, void* stream);
 
 /*
+ * Betweenness centrality on the SlimSell layout (an extension: the paper's
+ * conclusion names BC as an algorithm SlimSell can accelerate), by Brandes'
+ * dependency accumulation over a set of sources:
+ *   bc[v] = sum over s in sources, t != s, v of sigma_st(v) / sigma_st
+ * (sigma_st = number of shortest s-t paths, sigma_st(v) those through v).  On
+ * an undirected graph with every vertex as a source each unordered pair counts
+ * twice; halve for the one-direction convention.
+ * Per source: a forward pull per level over the rows not yet reached sums the
+ * path counts of neighbours one level up (the real-semiring BFS step with the
+ * counts kept), then a backward pull per level from the deepest level sums
+ * (1 + delta(w)) / sigma(w) over neighbours one level down.  fp64 throughout;
+ * split chunks (SlimChunk) combine with atomicAdd, so the result may differ
+ * from a serial sum in the last bits.
+ *   d_sources int32[k] device, k >= 1, each in [0, n) (copied to the host)
+ *   d_bc      double[n] device, overwritten
+ *   kernel_ms host double* or NULL: summed device time of the level kernels
+ * Synchronous with respect to the host.  Scratch (28 bytes per row) is
+ * allocated on first use and kept until slimsell_destroy.
+ * Errors: SS_ERR_INVALID (NULL, k < 1, a source out of range), SS_ERR_OOM,
+ *         SS_ERR_CUDA.
+ */
+ss_status slimsell_bc(slimsell_handle h, const int32_t* d_sources, int32_t k, double* d_bc,
+                      double* kernel_ms, void* stream);
+
+/*
  * Batched BFS over many graphs (an extension beyond the paper): one executable
  * CUDA graph holding, per handle, the chain init -> root -> device-side
  * iteration loop -> output, so that one launch runs every BFS and the chains

@@ -73,6 +73,7 @@ def lib():
         "slimsell_bfs_multi": (i32, [_VP, _VP, i32, i32, _VP, _VP]),
         "slimsell_bfs_multi_parents": (i32, [_VP, _VP, i32, i32, _VP, _VP, _VP]),
         "slimsell_bfs_spmv": (i32, [_VP, i32, i32, i32, _VP, ctypes.POINTER(ctypes.c_double), _VP]),
+        "slimsell_bc": (i32, [_VP, _VP, i32, _VP, ctypes.POINTER(ctypes.c_double), _VP]),
         "slimsell_get_info": (i32, [_VP, ctypes.POINTER(ss_info)]),
         "slimsell_get_run_stats": (i32, [_VP, ctypes.POINTER(ss_run_stats),
                                          ctypes.POINTER(ss_iter_stats), i32]),
@@ -103,7 +104,7 @@ def lib():
 
 def exported_symbols() -> list[str]:
     return ["slimsell_build", "slimsell_bfs", "slimsell_bfs_multi", "slimsell_bfs_multi_parents",
-            "slimsell_bfs_spmv",
+            "slimsell_bfs_spmv", "slimsell_bc",
             "slimsell_get_info", "slimsell_get_run_stats",
             "slimsell_set_profiling", "slimsell_set_option", "slimsell_export_layout",
             "slimsell_destroy",
@@ -171,6 +172,16 @@ def slimsell_bfs_spmv(h: int, root: int, semiring: int, fmt: int, dist: torch.Te
     ms = ctypes.c_double(0.0)
     _check("slimsell_bfs_spmv", lib().slimsell_bfs_spmv(
         h, int(root), int(semiring), int(fmt), _ptr(dist, torch.int32, "dist"),
+        ctypes.byref(ms) if timed else None, _stream(stream)))
+    return ms.value if timed else None
+
+
+def slimsell_bc(h: int, sources: torch.Tensor, bc: torch.Tensor, stream=None, timed: bool = False):
+    """Betweenness centrality over `sources` into `bc` (float64, length n);
+    returns the summed device time of its kernels in ms when timed, else None."""
+    ms = ctypes.c_double(0.0)
+    _check("slimsell_bc", lib().slimsell_bc(
+        h, _ptr(sources, torch.int32, "sources"), int(sources.numel()), _ptr(bc, torch.float64, "bc"),
         ctypes.byref(ms) if timed else None, _stream(stream)))
     return ms.value if timed else None
 
@@ -355,6 +366,14 @@ class SlimSellGraph:
             dist = torch.empty(self.n, dtype=torch.int32, device=torch.device("cuda", torch.cuda.current_device()))
         slimsell_bfs_spmv(self.h, root, sr, f, dist, stream)
         return dist
+
+    def bc(self, sources, stream=None):
+        """Betweenness centrality summed over `sources`; returns a float64 tensor."""
+        dev = torch.device("cuda", torch.cuda.current_device())
+        src = torch.as_tensor(sources, dtype=torch.int32).to(dev)
+        out = torch.empty(self.n, dtype=torch.float64, device=dev)
+        slimsell_bc(self.h, src, out, stream)
+        return out
 
     def bfs_multi_parents(self, roots, policy="slimwork", dist=None, parent=None,
                           want_dist: bool = True, stream=None):

@@ -582,10 +582,12 @@ static ss_status alloc_state(slimsell_graph* h) {
 }
 
 void ab_release(slimsell_graph* h);  // format-comparison scratch (ss_sell.cu)
+void bc_release(slimsell_graph* h);  // betweenness-centrality scratch (ss_bc.cu)
 
 void free_handle(slimsell_graph* h) {
   if (!h) return;
   ab_release(h);
+  bc_release(h);
   void* ptrs[] = {h->perm, h->invperm, h->rdeg, h->cl, h->cs, h->col, h->items, h->split_n,
                   h->lvl, h->act, h->fb[0], h->fb[1], h->fr, h->par, h->xacc, h->xpar,
                   h->arrive, h->ctl, h->iters, h->units, h->pbest,

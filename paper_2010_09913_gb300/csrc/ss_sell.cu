@@ -184,17 +184,16 @@ ss_status ab_scratch(slimsell_graph* h, bool sell, cudaStream_t st, AbScratch** 
   AbScratch& a = g_ab[h];
   ss_status s;
   const size_t np = (size_t)h->n_pad;
-  if (!a.acc) {
-    for (int b = 0; b < 2; ++b)
-      if ((s = dmalloc(h, (void**)&a.x[b], sizeof(float) * np)) != SS_OK) return s;
-    if ((s = dmalloc(h, (void**)&a.acc, sizeof(float) * np)) != SS_OK) return s;
-    if ((s = dmalloc(h, (void**)&a.lvl, sizeof(int) * np)) != SS_OK) return s;
-    if ((s = dmalloc(h, (void**)&a.cnt, sizeof(unsigned long long))) != SS_OK) return s;
-  }
-  if (sell && !a.scol) {
+  // allocate whatever is missing (also after a failed earlier call)
+  for (int b = 0; b < 2; ++b)
+    if (!a.x[b] && (s = dmalloc(h, (void**)&a.x[b], sizeof(float) * np)) != SS_OK) return s;
+  if (!a.acc && (s = dmalloc(h, (void**)&a.acc, sizeof(float) * np)) != SS_OK) return s;
+  if (!a.lvl && (s = dmalloc(h, (void**)&a.lvl, sizeof(int) * np)) != SS_OK) return s;
+  if (!a.cnt && (s = dmalloc(h, (void**)&a.cnt, sizeof(unsigned long long))) != SS_OK) return s;
+  if (sell && !a.vmul) {  // vmul is written last: its presence means the arrays are built
     const size_t slots = (size_t)(h->slots > 0 ? h->slots : 1);
-    if ((s = dmalloc(h, (void**)&a.scol, sizeof(int) * slots)) != SS_OK) return s;
-    if ((s = dmalloc(h, (void**)&a.vtrop, sizeof(float) * slots)) != SS_OK) return s;
+    if (!a.scol && (s = dmalloc(h, (void**)&a.scol, sizeof(int) * slots)) != SS_OK) return s;
+    if (!a.vtrop && (s = dmalloc(h, (void**)&a.vtrop, sizeof(float) * slots)) != SS_OK) return s;
     if ((s = dmalloc(h, (void**)&a.vmul, sizeof(float) * slots)) != SS_OK) return s;
     if (h->slots > 0) {
       k_sell_arrays<<<8 * h->num_sms, 256, 0, st>>>(h->col, h->slots, a.scol, a.vtrop, a.vmul);
