@@ -162,7 +162,7 @@ def sum_over_ranks(pg, x: float, device=None) -> float:
 
 
 def _oracle_warm(_):
-    import oracle  # the import and library load, outside the timed rounds
+    import oracle  # the import and library load, outside the timed batches
     oracle.build()
     time.sleep(0.2)  # hold this worker so that every worker gets one
     return 0
@@ -197,11 +197,11 @@ class OraclePool:
         self.pool = mp.get_context("spawn").Pool(self.workers)
         self.pool.map(_oracle_warm, range(self.workers), chunksize=1)
 
-    def rounds(self, tasks, cpu_budget_s: float):
-        """Run tasks a round (one per worker) at a time until the CPU seconds reach
-        the budget (at least one round): (edges, wall seconds, cpu seconds, runs)."""
+    def run_for(self, tasks, cpu_seconds: float):
+        """Run tasks in batches (one per worker) until the CPU seconds spent reach
+        `cpu_seconds` (at least one batch): (edges, wall seconds, cpu seconds, runs)."""
         edges, wall, cpu, runs, i = 0, 0.0, 0.0, 0, 0
-        while runs == 0 or (cpu < cpu_budget_s and runs < 1_000_000):  # tasks cycle
+        while runs == 0 or (cpu < cpu_seconds and runs < 1_000_000):  # tasks cycle
             batch = [tasks[(i + j) % len(tasks)] for j in range(self.workers)]
             i += self.workers
             t0 = time.perf_counter()
@@ -222,13 +222,13 @@ def oracle_workers() -> int:
     return max(1, min(8, os.cpu_count() or 1))
 
 
-def cpu_oracle_sample(g, roots, cpu_budget_s: float):
+def cpu_oracle_sample(g, roots, cpu_seconds: float):
     """Time the oracle (all four semirings, DP parents) on the host cores over a
     bounded sample of the workload's runs."""
     pool = OraclePool(g, oracle_workers())
     try:
         tasks = [(int(r), sr) for r in roots for sr in SEMIRINGS]
-        edges, wall, cpu, runs = pool.rounds(tasks, cpu_budget_s)
+        edges, wall, cpu, runs = pool.run_for(tasks, cpu_seconds)
     finally:
         pool.close()
     return edges, wall, cpu, runs, pool.workers
@@ -247,7 +247,7 @@ def run_reference(args, world, rank, pg):
     try:
         for s in range(args.warmup + args.steps):
             k = (s * pool.workers) % len(tasks)
-            edges, wall, cpu, runs = pool.rounds(tasks[k:] + tasks[:k], per_step)
+            edges, wall, cpu, runs = pool.run_for(tasks[k:] + tasks[:k], per_step)
             if s >= args.warmup:
                 times.append(wall)
                 edges_l.append(edges)

@@ -390,7 +390,7 @@ static ss_status make_items(slimsell_graph* h, int W, long long* tmp_cnt, long l
 // Order the BFS work items for the iteration kernels, whose warp w takes items
 // w, w + W, w + 2W, ... (W = warps in the grid): items are sorted by estimated
 // cost (slots plus a fixed per-item overhead), largest first, and every other
-// round of W items is reversed ("snake" order) so each warp's total is balanced.
+// group of W items is reversed ("snake" order) so each warp's total is balanced.
 static ss_status order_items(slimsell_graph* h, cudaStream_t st) {
   const int n = h->n_items;
   if (n <= 1) return SS_OK;

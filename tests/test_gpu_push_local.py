@@ -56,7 +56,7 @@ def grow_shrink(tail=300, fan=70000, seed=2):
 
 
 def wide_star(tail=200, leaves=140000, seed=3):
-    """A path ending in a hub whose degree alone exceeds the block's edge budget."""
+    """A path ending in a hub whose degree alone exceeds the block's edge capacity."""
     e = [(i, i + 1) for i in range(tail)]
     hub = tail
     e += [(hub, hub + 1 + j) for j in range(leaves)]
@@ -125,7 +125,7 @@ def test_hand_over_both_ways(policy, loop):
 
 
 @pytest.mark.parametrize("loop", [1, 0])
-def test_edge_budget_hand_back(loop):
+def test_edge_capacity_hand_back(loop):
     g, p = wide_star()
     G = ss.SlimSellGraph.from_host(g.row_ptr, g.col, C=32, sigma=g.n, split_w=256)
     G.set_option(ss.OPT_DEVICE_LOOP, loop)
