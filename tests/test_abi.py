@@ -63,3 +63,19 @@ def test_null_handle_rejected(lib):
     assert lib.slimsell_get_info(None, None) == 1
     assert lib.slimsell_set_profiling(None, 1) == 1
     lib.slimsell_destroy(None)  # no-op
+
+
+def test_extension_entry_points_reject_null_on_host(lib):
+    """Multi-source BFS (with and without parents), the format comparison and
+    betweenness centrality refuse a NULL handle or output before any CUDA call."""
+    fake = ctypes.c_void_p(16)  # never dereferenced: validation fails first
+    assert lib.slimsell_bfs_multi(None, fake, 4, 1, None, None) == 1
+    assert lib.slimsell_bfs_multi_parents(None, fake, 4, 1, None, fake, None) == 1
+    assert lib.slimsell_bfs_multi_parents(fake, None, 4, 1, None, None, None) == 1
+    assert "NULL" in ss.slimsell_last_error()
+    assert lib.slimsell_bfs_spmv(None, 0, 0, 0, fake, None, None) == 1
+    assert lib.slimsell_bfs_spmv(fake, 0, 0, 0, None, None, None) == 1
+    assert lib.slimsell_bc(None, fake, 1, fake, None, None) == 1
+    assert lib.slimsell_bc(fake, None, 1, fake, None, None) == 1
+    assert lib.slimsell_bc(fake, fake, 1, None, None, None) == 1
+    assert "NULL" in ss.slimsell_last_error()
