@@ -2,7 +2,10 @@
 SlimChunk width w) of a graph: builds the layout for every point of a grid,
 times BFS on sample roots with CUDA events (device-side loops), and keeps the
 fastest.  Results are cached by a graph signature (n, nnz, log2 degree
-histogram), so graphs of the same family and size reuse one search.
+histogram); a graph reuses a cached search when its n and rounded nnz match and
+its histogram is within HIST_TOLERANCE (L1, in histogram units) of the cached
+one, so graphs of the same family and size share one search even where the
+coarse histogram buckets of two seeds fall on opposite sides of a bucket edge.
 """
 from __future__ import annotations
 
@@ -14,6 +17,7 @@ from . import (POLICIES, SEMIRINGS, slimsell_bfs, slimsell_build, slimsell_destr
 GRID = {"C": (8, 16, 32, 64), "sigma": (1, 256, 4096, "n"), "split_w": (256, 1024, 4096)}
 
 _cache: dict = {}
+HIST_TOLERANCE = 3
 
 
 def signature(row_ptr: np.ndarray) -> tuple:
@@ -24,13 +28,38 @@ def signature(row_ptr: np.ndarray) -> tuple:
     return (n, round(nnz, -max(0, len(str(nnz)) - 2)), tuple(int(round(h / max(1, n) * 50)) for h in hist))
 
 
+def grid_key(grid) -> tuple:
+    return tuple(sorted((k, tuple(v)) for k, v in grid.items()))
+
+
+def lookup(cache: dict, key):
+    """The cached entry for `key` = (signature, semiring, policy[, grid key]): an
+    exact match, else the closest cached signature with the same n, rounded nnz
+    and the same remaining fields whose histogram differs by at most
+    HIST_TOLERANCE (L1); None if none."""
+    if key in cache:
+        return cache[key]
+    (n, nnz, hist), rest = key[0], key[1:]
+    best, best_d = None, HIST_TOLERANCE + 1
+    for k, entry in cache.items():
+        sig = k[0]
+        if k[1:] != rest or sig[0] != n or sig[1] != nnz:
+            continue
+        d = sum(abs(a - b) for a, b in zip(sig[2], hist))
+        if d < best_d:
+            best, best_d = entry, d
+    return best
+
+
 def tune(row_ptr: np.ndarray, col: np.ndarray, roots, semiring: str = "tropical",
          policy: str = "slimwork", grid=GRID, repeats: int = 2, use_cache: bool = True,
          device="cuda"):
     """Returns (best {C, sigma, split_w}, [(params, ms per BFS), ...])."""
-    key = (signature(row_ptr), semiring, policy)
-    if use_cache and key in _cache:
-        return _cache[key]
+    key = (signature(row_ptr), semiring, policy, grid_key(grid))
+    if use_cache:
+        hit = lookup(_cache, key)
+        if hit is not None:
+            return hit
     n = len(row_ptr) - 1
     rp = torch.from_numpy(np.asarray(row_ptr, dtype=np.int64)).to(device)
     cl = torch.from_numpy(np.asarray(col, dtype=np.int32)).to(device)
