@@ -54,7 +54,7 @@ def collect(G, roots, semiring: str = "tropical", repeats: int = 3, max_per_root
             runs = [_profiled_run(G, int(r), semiring, v) for _ in range(repeats)]
             ns = np.median(np.stack([x[0] for x in runs]), axis=0)
             executed = runs[0][1]
-            ok = (executed == vi) | ((vi == 2) & (executed == 4))  # 4: single-block push
+            ok = (executed == vi) | ((vi == 2) & (executed == 4))  # 4: cluster push
             per_var.append((ns, ok))
             if v == "pull_filtered":
                 feats = runs[0][2]

@@ -164,7 +164,7 @@ def test_sparse_families_device_vs_host_loop(maker):
 
 
 def test_alternating_policies_keep_scratch_clean():
-    """Pull, single-block push and grid push share the frontier bitmaps and push
+    """Pull, cluster push and grid push share the frontier bitmaps and push
     scratch; alternating runs on one handle must not leak state between runs."""
     g, p = grow_shrink(tail=120, fan=66000, seed=7)
     G = ss.SlimSellGraph.from_host(g.row_ptr, g.col, C=32, sigma=g.n, split_w=256)
