@@ -38,10 +38,10 @@ FRONTIER_BYTES = {"tropical": 4.0, "real": 4.0, "boolean": 0.125, "selmax": 4.0}
 FRONTIER_WRITE = {"tropical": 0.0, "real": 4.0, "boolean": 0.125, "selmax": 4.0}
 
 # DRAM traffic per k_pull launch measured by ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum, mean over the 56 tropical iterations of the first 8 roots
-# of this workload; profiles/k_pull_kron22.md), keyed by the hash of the kernel
-# sources it was taken on; reported as null once those sources change.
-NCU_TRAFFIC = {"854684db07ad1a3f": 238.0e6}  # profiles/k_pull_kron22.md
+# dram__bytes_write.sum, mean over the tropical iterations of the first 8 roots
+# of this workload, taken with --clock-control none), keyed by the hash of the
+# kernel sources it was taken on; reported as null once those sources change.
+NCU_TRAFFIC = {"854684db07ad1a3f": 238.0e6}
 KERNEL_SOURCES = ["ss_bfs.cu", "ss_device.cuh", "ss_common.cuh"]
 
 
@@ -178,21 +178,27 @@ def _oracle_warm(_):
 
 
 def _oracle_task(task):
-    """One oracle BFS in a worker process: (edges reached, seconds)."""
-    path, root, sr = task
+    """One oracle run in a worker process: (edges reached, seconds).  kind
+    "queue": the serial queue BFS plus the max-id parent pass (the CPU
+    baseline); kind "semiring": the plain CSR semiring BFS of that semiring."""
+    path, root, sr, kind = task
     import oracle
     row_ptr = np.load(os.path.join(path, "row_ptr.npy"), mmap_mode="r")
     col = np.load(os.path.join(path, "col.npy"), mmap_mode="r")
     t0 = time.perf_counter()
-    dist = oracle.bfs_semiring(row_ptr, col, int(root), sr)[0]
+    if kind == "queue":
+        dist = oracle.bfs_queue(row_ptr, col, int(root))
+        oracle.dp(row_ptr, col, dist, int(root))
+    else:
+        dist = oracle.bfs_semiring(row_ptr, col, int(root), sr)[0]
     dt = time.perf_counter() - t0
     return oracle.reached_edges(row_ptr, dist), dt
 
 
 class OraclePool:
-    """The oracle's plain CSR semiring BFS run on the host cores, one serial BFS
-    per worker process (spawned, so no CUDA state is inherited); the CSR goes to
-    the workers through memory-mapped files."""
+    """The oracle run on the host cores, one serial run per worker process
+    (spawned, so no CUDA state is inherited); the CSR goes to the workers
+    through memory-mapped files."""
 
     def __init__(self, g, workers: int):
         import multiprocessing as mp
@@ -206,15 +212,17 @@ class OraclePool:
         self.pool = mp.get_context("spawn").Pool(self.workers)
         self.pool.map(_oracle_warm, range(self.workers), chunksize=1)
 
-    def run_for(self, tasks, cpu_seconds: float):
-        """Run tasks in batches (one per worker) until the CPU seconds spent reach
-        `cpu_seconds` (at least one batch): (edges, wall seconds, cpu seconds, runs)."""
+    def run_for(self, tasks, cpu_seconds: float, kind: str = "queue", per_batch: int | None = None):
+        """Run tasks in batches of `per_batch` (default: one per worker) until
+        the CPU seconds spent reach `cpu_seconds` (at least one batch):
+        (edges, wall seconds, cpu seconds, runs)."""
+        per_batch = self.workers if per_batch is None else max(1, min(per_batch, self.workers))
         edges, wall, cpu, runs, i = 0, 0.0, 0.0, 0, 0
         while runs == 0 or (cpu < cpu_seconds and runs < 1_000_000):  # tasks cycle
-            batch = [tasks[(i + j) % len(tasks)] for j in range(self.workers)]
-            i += self.workers
+            batch = [tasks[(i + j) % len(tasks)] for j in range(per_batch)]
+            i += per_batch
             t0 = time.perf_counter()
-            res = self.pool.map(_oracle_task, [(self.dir, r, sr) for r, sr in batch], chunksize=1)
+            res = self.pool.map(_oracle_task, [(self.dir, r, sr, kind) for r, sr in batch], chunksize=1)
             wall += time.perf_counter() - t0
             edges += sum(e for e, _ in res)
             cpu += sum(t for _, t in res)
@@ -228,19 +236,23 @@ class OraclePool:
 
 
 def oracle_workers() -> int:
-    return max(1, min(8, os.cpu_count() or 1))
+    """Every host core (one serial oracle run per core)."""
+    return max(1, os.cpu_count() or 1)
 
 
 def cpu_oracle_sample(g, roots, cpu_seconds: float):
-    """Time the oracle (all four semirings, DP parents) on the host cores over a
-    bounded sample of the workload's runs."""
+    """Time the oracle on the host cores over bounded samples of the workload's
+    runs: the serial queue BFS plus max-id parent pass (every core, batches of
+    one run per core until `cpu_seconds` of CPU time), and the plain CSR
+    semiring BFS (one root, its four semirings run side by side)."""
     pool = OraclePool(g, oracle_workers())
     try:
         tasks = [(int(r), sr) for r in roots for sr in SEMIRINGS]
-        edges, wall, cpu, runs = pool.run_for(tasks, cpu_seconds)
+        queue = pool.run_for(tasks, cpu_seconds, "queue")
+        semiring = pool.run_for(tasks[:4], 0.0, "semiring", per_batch=4)
     finally:
         pool.close()
-    return edges, wall, cpu, runs, pool.workers
+    return queue, semiring, pool.workers
 
 
 def run_reference(args, world, rank, pg):
@@ -256,7 +268,7 @@ def run_reference(args, world, rank, pg):
     try:
         for s in range(args.warmup + args.steps):
             k = (s * pool.workers) % len(tasks)
-            edges, wall, cpu, runs = pool.run_for(tasks[k:] + tasks[:k], per_step)
+            edges, wall, cpu, runs = pool.run_for(tasks[k:] + tasks[:k], per_step, "queue")
             if s >= args.warmup:
                 times.append(wall)
                 edges_l.append(edges)
@@ -265,12 +277,13 @@ def run_reference(args, world, rank, pg):
         pool.close()
     value = sum(edges_l) / sum(times) / 1e9
     ms = 1000.0 * sum(times) / len(times)
-    sample = (f"oracle semiring BFS (plain CSR, fp64, serial C per run), all 4 semirings per root, "
-              f"one run per worker process on {pool.workers} host cores, ~{per_step:.0f} CPU-seconds "
-              f"per step on kronecker scale {args.scale}")
+    sample = (f"oracle serial queue BFS + max-id parent pass (C, one run per (root, semiring) of "
+              f"the workload; the four semirings give the same dist/parent), one run per worker "
+              f"process on {pool.workers} host cores, ~{per_step:.0f} CPU-seconds per step on "
+              f"kronecker scale {args.scale}")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GTEPS",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic",
             "config": workload_config(args, g),
             "cpu_baseline": {"kind": "oracle", "cores": pool.workers, "sample": sample, "value": value,
@@ -393,10 +406,12 @@ def batched_learned(ss, torch, g, h, roots, args, stream, dev, runs_edges):
     return out
 
 
-def batched_graphs(ss, torch, ngraphs, stream, dev):
-    """Many Kronecker graphs of uneven size (scales drawn from 10..18), one root
-    each: layout parameters autotuned once per scale, then every BFS one after
-    another vs all of them in one CUDA-graph launch."""
+def batch_workload(ss, torch, ngraphs, stream, dev):
+    """The many-graph configuration: `ngraphs` Kronecker graphs with scales drawn
+    uniformly from 10..18 (seeded), layout parameters autotuned once per scale
+    (C x sigma x split width grid, tropical SlimWork timings), one handle per
+    graph and one seeded root each.  Returns (graphs, scales, handles, roots,
+    tuned, autotune seconds)."""
     from paper_2010_09913_gb300 import autotune
     rng = np.random.default_rng(17)
     scales = rng.integers(10, 19, ngraphs)
@@ -417,6 +432,14 @@ def batched_graphs(ss, torch, ngraphs, stream, dev):
         sigma = g.n if p["sigma"] == "n" else int(p["sigma"])
         handles.append(ss.slimsell_build(rp, cl, g.n, g.nnz, p["C"], sigma, p["split_w"], stream))
     roots = [int(gg.roots(g, 1, seed=2)[0]) for g in graphs]
+    return graphs, scales, handles, roots, tuned, tune_s
+
+
+def batched_graphs(ss, torch, ngraphs, stream, dev):
+    """Many Kronecker graphs of uneven size (scales drawn from 10..18), one root
+    each: layout parameters autotuned once per scale, then every BFS one after
+    another vs all of them in one CUDA-graph launch."""
+    graphs, scales, handles, roots, tuned, tune_s = batch_workload(ss, torch, ngraphs, stream, dev)
     r_d = torch.tensor(roots, dtype=torch.int32, device=dev)
     out = {"graphs": ngraphs, "scales": {int(s): int((scales == s).sum()) for s in sorted(set(scales))},
            "tuned": {str(k): v for k, v in tuned.items()}, "autotune_seconds": tune_s,
@@ -470,7 +493,7 @@ def roofline_at_scale(ss, torch, scale, nroots, split_w, stream, dev):
     del rp_d, col_d
     hbm, kind = load_peaks()
     out = {"graph": f"kronecker scale {scale}", "n": g.n, "nnz": g.nnz, "roots": nroots}
-    for sr in ("tropical", "boolean"):
+    for sr in SEMIRINGS:
         ss.slimsell_set_profiling(h, True)
         bytes_, ms_, edges = 0.0, 0.0, 0
         for r in roots:
@@ -580,19 +603,21 @@ def format_ab_sections(ss, torch, stream, dev, g22=None):
 
 def selector_heldout(ss, torch, stream, dev, weights):
     """The selector trained above, on graphs it never saw: Kronecker scale 25
-    (edgefactor 16) and a 8192 x 8192 lattice with 5% of its edges deleted;
-    tropical; learned against the frontier-size rule and plain SlimWork."""
+    (edgefactor 16) and a 8192 x 8192 lattice with 5% of its edges deleted, 64
+    seeded roots each; tropical; learned against the frontier-size rule and
+    plain SlimWork (plain SlimWork on the lattice on a 2-root sample: one run
+    takes seconds there)."""
     out = {}
     for name, g, nr, nplain in (("kronecker scale 25", gg.kronecker(25, seed=3), 64, 64),
-                                ("lattice 8192^2 (5% deleted)", gg.lattice(8192, 0.05, seed=3), 8, 1)):
+                                ("lattice 8192^2 (5% deleted)", gg.lattice(8192, 0.05, seed=3), 64, 2)):
         roots = gg.roots(g, nr, seed=4)
         rp_d = torch.from_numpy(g.row_ptr).to(dev)
         col_d = torch.from_numpy(g.col).to(dev)
         h = ss.slimsell_build(rp_d, col_d, g.n, g.nnz, 32, g.n, 256, stream)
+        res = {"roots": nr, "n": int(g.n), "nnz": int(g.nnz)}
         del rp_d, col_d, g
         ss.slimsell_selector_load(h, weights)
         ss.slimsell_set_option(h, ss.OPT_SELECTOR_MARGIN, SELECTOR_MARGIN)
-        res = {"roots": nr}
         for pol_name, pol, rs in (("learned", ss.V_LEARNED, roots), ("heuristic", ss.V_HEURISTIC, roots),
                                   ("slimwork", ss.V_SLIMWORK, roots[:nplain])):
             ss.slimsell_bfs(h, int(rs[0]), SR_ID["tropical"], pol, None, None, stream)  # warm-up
@@ -608,8 +633,45 @@ def selector_heldout(ss, torch, stream, dev, weights):
                 ms += e0.elapsed_time(e1)
                 edges += ss.slimsell_get_run_stats(h)[0].reached_degree // 2
             res[pol_name] = {"gteps": edges / (ms / 1000.0) / 1e9, "ms_per_run": ms / len(rs), "runs": len(rs)}
+        res["learned_over_heuristic"] = res["learned"]["gteps"] / res["heuristic"]["gteps"]
+        res["learned_over_slimwork"] = res["learned"]["gteps"] / res["slimwork"]["gteps"]
         ss.slimsell_destroy(h)
         out[name] = res
+    return out
+
+
+def summary(line):
+    """Compact digest of the sections, printed as the line's last key (a reader
+    that keeps only the end of the output still sees it)."""
+    def r3(x):
+        return None if x is None else float(f"{x:.4g}")
+    out = {}
+    if "per_semiring" in line:
+        out["kron22_gteps"] = {sr: r3(v["gteps"]) for sr, v in line["per_semiring"].items()}
+        out["kron22_whole_run_hbm_frac"] = {sr: r3(v["whole_run_hbm_frac"])
+                                            for sr, v in line["per_semiring"].items()}
+    if "scale24" in line:
+        out["kron24_k_pull_hbm_frac"] = {sr: r3(line["scale24"][sr]["hbm_frac"]) for sr in SEMIRINGS}
+    bl = line.get("batched_learned")
+    if bl:
+        out["kron22_single"] = {k: r3(bl[k]) for k in ("plain_slimwork_single", "heuristic_single",
+                                                       "learned_single")}
+        out["kron22_multi"] = {k: r3(bl[f"multi_{k}"]) for k in (64, 256, 1024)}
+        out["best_batched_or_learned_over_plain"] = r3(bl["best_batched_or_learned_over_plain"])
+    ho = line.get("selector_heldout")
+    if ho:
+        out["heldout"] = {name.split(" (")[0]: {p: r3(v[p]["gteps"]) for p in ("learned", "heuristic",
+                                                                              "slimwork")}
+                          for name, v in ho.items()}
+    hd = line.get("high_diameter")
+    if hd:
+        out["high_diameter_tropical"] = {name.split(" (")[0]: {p: r3(v[f"tropical_{p}"]["gteps"])
+                                                              for p in ("heuristic", "learned", "slimwork")
+                                                              if f"tropical_{p}" in v}
+                                         for name, v in hd.items()}
+    bg = line.get("batched_graphs")
+    if bg:
+        out["batch200"] = {k: r3(bg[k]) for k in ("batch_slimwork", "batch_heuristic", "sequential_slimwork")}
     return out
 
 
@@ -688,8 +750,8 @@ def main():
                     help="run one section alone and print it (profiling runs)")
     ap.add_argument("--host-loop", action="store_true",
                     help="host-driven iteration loop (kernels visible to a profiler)")
-    ap.add_argument("--selector-heldout", action="store_true",
-                    help="also evaluate the selector on held-out Kronecker 25 and lattice 8192^2")
+    ap.add_argument("--no-heldout", action="store_true",
+                    help="skip the selector's held-out evaluation (Kronecker 25, lattice 8192^2)")
     ap.add_argument("--batch-graphs", type=int, default=200)
     args = ap.parse_args()
     world, rank, local, pg = dist_setup()
@@ -839,6 +901,9 @@ def main():
                          "traffic": traffic,
                          "algorithmic_bytes_per_launch": pull_bytes_per_step / max(1, pull_launches_per_step),
                          "avg_launch_ms": pull_ms / max(1, pull_launches_per_step),
+                         "launch_timing": "one step through the host-driven iteration loop (same "
+                                          "kernels as the timed device-side loop), CUDA events on "
+                                          "the launching stream around every k_pull launch",
                          "frac_of_nominal_8tbs": achieved / 8000.0},
             "per_semiring": per_sr, "clocks": clk,
             "build_ms": build_ms,
@@ -862,24 +927,36 @@ def main():
     if not args.no_scale24 and rank == 0:
         torch.cuda.empty_cache()
         line["scale24"] = roofline_at_scale(ss, torch, 24, 8, args.split_w, stream, dev)
+        # the single-source roofline target is set on this graph: carry its
+        # per-semiring fractions in the roofline object itself
+        line["roofline"]["scale24_frac"] = {sr: line["scale24"][sr]["hbm_frac"] for sr in SEMIRINGS}
+        line["roofline"]["scale24_frac_min"] = min(line["roofline"]["scale24_frac"].values())
     if not args.no_format_ab and rank == 0:
         torch.cuda.empty_cache()
         line["format_ab"] = format_ab_sections(ss, torch, stream, dev, g)
     if not args.no_high_diameter and rank == 0:
         torch.cuda.empty_cache()
         line["high_diameter"] = high_diameter(ss, torch, stream, dev, sel_w)
-    if args.selector_heldout and rank == 0 and sel_w is not None:
+    if not args.no_heldout and rank == 0 and sel_w is not None:
         torch.cuda.empty_cache()
         line["selector_heldout"] = selector_heldout(ss, torch, stream, dev, sel_w)
     if rank == 0 and world == 1 and not args.no_cpu:
-        edges, wall, cpu, nruns, workers = cpu_oracle_sample(g, roots, 20.0)
+        (edges, wall, cpu, nruns), (s_edges, s_wall, s_cpu, s_runs), workers = \
+            cpu_oracle_sample(g, roots, 20.0)
         line["cpu_baseline"] = {"value": edges / wall / 1e9, "unit": "GTEPS", "cores": workers,
                                 "kind": "oracle",
-                                "sample": f"{nruns} runs (roots x 4 semirings) of the oracle's plain "
-                                          f"CSR semiring BFS on kronecker scale {args.scale}, one serial "
-                                          f"run per worker process, {cpu:.0f} CPU-seconds in "
-                                          f"{wall:.1f} s"}
+                                "sample": f"{nruns} runs (roots x 4 semirings) of the oracle's serial "
+                                          f"queue BFS + max-id parent pass on kronecker scale "
+                                          f"{args.scale}, one run per worker process on every host "
+                                          f"core, {cpu:.0f} CPU-seconds in {wall:.1f} s",
+                                "semiring_bfs": {"value": s_edges / s_wall / 1e9, "unit": "GTEPS",
+                                                 "cores": min(4, workers),
+                                                 "sample": f"{s_runs} runs (one root x 4 semirings) of "
+                                                           f"the oracle's plain CSR semiring BFS (fp64), "
+                                                           f"side by side, {s_cpu:.0f} CPU-seconds in "
+                                                           f"{s_wall:.1f} s"}}
     if rank == 0:
+        line["summary"] = summary(line)
         print(json.dumps(line), flush=True)
     if pg is not None:
         pg.destroy_process_group()

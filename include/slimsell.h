@@ -327,13 +327,17 @@ ss_status slimsell_export_layout(slimsell_handle h, int32_t* d_perm, int32_t* d_
  * allocation and no freeing.  Its scratch is one fixed device array of about
  * 12.3 MiB that every GPU loading the library holds until the process exits.
  *   d_row_ptr  int64[n + 1] CSR offsets (degrees must be below n, i.e. no
- *              duplicate entries or self-loops), device memory, not modified.
+ *              duplicate entries or self-loops; a larger degree is clamped to
+ *              2^19 - 1 in the sort key), device memory, not modified.
  *   n          1 <= n <= 524288 (2^19); larger n returns SS_ERR_INVALID.
  *   sigma      >= 1.
  *   d_perm     int32[n] output, device memory owned by the caller.
- * Stream-ordered and asynchronous: it returns after queueing its kernels.  The
- * first call on a device looks up the array's device address (once per device,
- * with that device current); make that first call before any stream capture.
+ * Stream-ordered and asynchronous: it returns after queueing its kernels.  Each
+ * call made outside stream capture looks up the array's device address on the
+ * current device (so a context reset, which may move the array, is followed);
+ * a call made while `stream` is being captured reuses the address of the last
+ * lookup on that device, so make the first call on a device before any stream
+ * capture (a first call during capture returns SS_ERR_INVALID).
  * All calls share the one array and it keeps the last call's contents: calls
  * that overlap on the GPU (different streams, or different host threads
  * without ordering) race and corrupt each other's results, so order them.

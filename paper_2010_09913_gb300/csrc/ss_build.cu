@@ -234,7 +234,9 @@ __global__ void k_make_keys(const int* deg, int n, int sigma, int maxdeg, int db
   for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
        v += (long long)gridDim.x * blockDim.x) {
     unsigned long long win = (unsigned long long)(v / sigma);
-    keys[v] = (win << dbits) | (unsigned long long)(maxdeg - deg[v]);
+    // a degree above maxdeg (possible only for inputs that break the caller's
+    // contract) is clamped so that it cannot spill into the window bits
+    keys[v] = (win << dbits) | (unsigned long long)(maxdeg - min(deg[v], maxdeg));
     vals[v] = (int)v;
   }
 }

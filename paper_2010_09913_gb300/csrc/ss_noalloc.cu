@@ -36,20 +36,31 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 std::mutex g_mu;
 void* g_scratch_addr[256] = {};
 
-// Device address of the scratch on the current device, looked up once per device.
-ss_status scratch_address(unsigned char** out) {
+// Device address of the scratch on the current device.  Outside stream capture
+// it is looked up on every call: a context reset (cudaDeviceReset, or a reset of
+// the primary context by the host framework) unloads the module, and the array
+// may come back at another address.  While `st` is being captured the address
+// of the last lookup on this device is used (capture cannot span a reset), so
+// the first call on a device must come before any capture.
+ss_status scratch_address(cudaStream_t st, unsigned char** out) {
   int dev = 0;
   SS_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 256) {
     set_error("slimsell_sigma_sort_noalloc: device index %d out of range", dev);
     return SS_ERR_UNSUPPORTED;
   }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  SS_CUDA(cudaStreamIsCapturing(st, &cap));
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_addr[dev]) {
+  if (cap == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
     g_scratch_addr[dev] = p;
+  } else if (!g_scratch_addr[dev]) {
+    set_error("slimsell_sigma_sort_noalloc: first call on device %d made during stream capture; "
+              "call it once outside capture first", dev);
+    return SS_ERR_INVALID;
   }
   *out = static_cast<unsigned char*>(g_scratch_addr[dev]);
   return SS_OK;
@@ -85,9 +96,9 @@ extern "C" ss_status slimsell_sigma_sort_noalloc(const int64_t* d_row_ptr, int32
     return SS_ERR_INVALID;
   }
   unsigned char* base = nullptr;
-  ss_status s = scratch_address(&base);
-  if (s != SS_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
+  ss_status s = scratch_address(st, &base);
+  if (s != SS_OK) return s;
   int* deg = reinterpret_cast<int*>(base + OFF_DEG);
   unsigned long long* keys_a = reinterpret_cast<unsigned long long*>(base + OFF_KEYS_A);
   unsigned long long* keys_b = reinterpret_cast<unsigned long long*>(base + OFF_KEYS_B);
@@ -102,8 +113,9 @@ extern "C" ss_status slimsell_sigma_sort_noalloc(const int64_t* d_row_ptr, int32
     SS_CUDA(cudaGetLastError());
     return SS_OK;
   }
-  // the degree kernel folds a maximum into this slot, which keeps the last call's value
-  SS_CUDA(cudaMemsetAsync(maxdeg, 0, sizeof(int), st));
+  // the shared degree kernel also folds the largest degree into `maxdeg`; this
+  // call does not read it (the keys use a fixed 19-bit degree field, and
+  // k_make_keys clamps degrees to it), so the slot is never cleared
   k_degrees<<<grid, 256, 0, st>>>(reinterpret_cast<const long long*>(d_row_ptr), n, deg, maxdeg);
   const int window = sigma >= n ? n : sigma;
   const long long nwin = ((long long)n + window - 1) / window;

@@ -5,8 +5,10 @@ memory (device memory fully reserved by another allocator, or loops that cannot
 pay for cudaMalloc's synchronisation); it keeps its scratch in one fixed device
 array shared by all calls.  These tests call it through the C ABI twice in a
 row and compare each result with the permutation exported from a handle built
-by slimsell_build, exactly (the permutation is integer data).  They pass both
-alone in a fresh process and after the rest of the suite.
+by slimsell_build, exactly (the permutation is integer data); the cases at the
+array's size limit (n = 2^19, the widest keys) are also compared with the
+oracle's layout.  They pass both alone in a fresh process and after the rest of
+the suite.
 """
 import ctypes
 
@@ -15,6 +17,7 @@ import pytest
 import torch
 
 import graphgen as gg
+import oracle
 import paper_2010_09913_gb300 as ss
 
 pytestmark = pytest.mark.gpu
@@ -50,6 +53,22 @@ def test_noalloc_sort_matches_build_on_two_calls_in_a_row():
         want = reference_perm(g, sigma)
         first = noalloc_perm(g, sigma)
         second = noalloc_perm(g, sigma)  # the shared scratch keeps the last call's contents
+        np.testing.assert_array_equal(first, want)
+        np.testing.assert_array_equal(second, want)
+
+
+def test_noalloc_sort_at_the_size_limit():
+    """n = 2^19 exactly: the scratch offsets (histograms of 128 tiles, the scan's
+    partials) at their largest; sigma = 8 gives 65,536 windows, so the keys carry
+    19 + 16 bits and the sort makes five passes."""
+    ss.build()
+    g = gg.kronecker(19, seed=2)
+    assert g.n == MAX_N
+    for sigma in (g.n, 8):
+        want = oracle.slimsell_layout(g.row_ptr, g.col, 8, sigma)["perm"]
+        np.testing.assert_array_equal(reference_perm(g, sigma), want)
+        first = noalloc_perm(g, sigma)
+        second = noalloc_perm(g, sigma)
         np.testing.assert_array_equal(first, want)
         np.testing.assert_array_equal(second, want)
 
