@@ -147,8 +147,9 @@ ss_status slimsell_build(const int64_t* d_row_ptr, const int32_t* d_col, int32_t
  * By default the iterations run as a device-side loop (a conditional CUDA graph
  * that stops when an iteration discovers nothing) and the call returns once the
  * work is queued on `stream`; slimsell_get_run_stats waits for it.  With
- * profiling on (or SS_OPT_DEVICE_LOOP = 0) the host drives the loop, reading
- * one counter per iteration, and the call returns after the BFS has finished.
+ * profiling on (or SS_OPT_DEVICE_LOOP = 0) the host drives the loop (see
+ * SS_OPT_PROFILE_QUEUE for how often it reads the run's counter), and the call
+ * returns after the BFS has finished.
  * The outputs, and the handle's state, belong to this call until `stream`
  * reaches its end: do not start another call on the same handle from a
  * different stream before that.
@@ -291,9 +292,16 @@ typedef enum {
                              0 .. 212992 (default 212992); results do not depend on it          */
   SS_OPT_DEVICE_LOOP = 3, /* 1 (default): iterate on the device in a conditional CUDA graph;
                              0: the host launches each iteration and reads its counter          */
-  SS_OPT_SELECTOR_MARGIN = 4 /* learned policy, in thousandths of a log-time unit, 0 .. 100000
+  SS_OPT_SELECTOR_MARGIN = 4, /* learned policy, in thousandths of a log-time unit, 0 .. 100000
                              (default 0): the network's choice replaces the frontier-size rule's
                              only when it predicts a gain larger than this margin             */
+  SS_OPT_PROFILE_QUEUE = 5 /* host-driven loop (profiling on, or SS_OPT_DEVICE_LOOP = 0) with a
+                             fixed variant (FULL, SLIMWORK, PULL_FILTERED): 1 (default) queues
+                             the iterations eight at a time, each launch between its own pair of
+                             CUDA events, and reads the run's counter once per batch (launches
+                             past the end of the run return at once); 0: one launch, one event
+                             pair and one counter read per iteration, as for the adaptive
+                             policies                                                         */
 } ss_option;
 
 /* Set a handle option (applies to later calls).  Errors: SS_ERR_INVALID. */

@@ -203,7 +203,7 @@ def slimsell_set_profiling(h: int, on: bool) -> None:
     _check("slimsell_set_profiling", lib().slimsell_set_profiling(h, 1 if on else 0))
 
 
-OPT_DP_PASS, OPT_SMEM_BYTES, OPT_DEVICE_LOOP, OPT_SELECTOR_MARGIN = 1, 2, 3, 4
+OPT_DP_PASS, OPT_SMEM_BYTES, OPT_DEVICE_LOOP, OPT_SELECTOR_MARGIN, OPT_PROFILE_QUEUE = 1, 2, 3, 4, 5
 
 
 def slimsell_set_option(h: int, option: int, value: int) -> None:

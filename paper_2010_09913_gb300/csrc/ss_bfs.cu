@@ -67,6 +67,16 @@ constexpr unsigned long long STAGE_MIN_SLOTS = 2ull << 20;
 
 enum { MODE_FULL = 0, MODE_SLIMWORK = 1, MODE_FILTERED = 3 };
 
+// Real semiring: a level whose frontier's degree sum exceeds nnz / HUB_EDGE_SHARE
+// stages the values of the HUB_VALUE_ROWS highest-degree rows (64 KB) in shared
+// memory, where most of its value gathers land (the top 16 K rows of a
+// Kronecker graph of scale 22 receive 40 % of all edge endpoints).
+#ifndef SS_HUB_VALUE_ROWS
+#define SS_HUB_VALUE_ROWS 16384
+#endif
+constexpr int HUB_VALUE_ROWS = SS_HUB_VALUE_ROWS;
+constexpr unsigned long long HUB_EDGE_SHARE = 16;
+
 __device__ __forceinline__ int4 ld_stream(const int4* p) {
 #if SS_PULL_LOAD == 1
   int4 v;
@@ -229,21 +239,29 @@ __device__ __forceinline__ void carry_chunk(const Dev& d, int k, int chunk, int 
 // Scan the slots of one quad: record the first frontier hit per row and, for
 // the real semiring, add the values of all hits.
 // live: bit r set while row r is unvisited.  Visited rows keep their value, so
-// the real semiring gathers frontier values for live rows only.  (Skipping the
-// bit lookups of rows already hit, for the other semirings, measured slower:
-// the predicated lookups cost more issue slots than they save.)
+// the real semiring gathers frontier values for live rows only, and only in a
+// branch taken when a live row of the quad was hit (the full passes of the first
+// levels see almost no hits).  Values of rows below sf come from the copy staged
+// in shared memory (smf), the others from global memory.  (Skipping the bit
+// lookups of rows already hit, for the other semirings, measured slower: the
+// predicated lookups cost more issue slots than they save.)
 template <int SR>
 __device__ __forceinline__ void scan_quad(const Dev& d, const unsigned* sm, int sbits,
                                           const unsigned* gbm, int4 c, int first[4], float sum[4],
-                                          unsigned live) {
+                                          unsigned live, const float* smf, int sf) {
   const int cc[4] = {c.x, c.y, c.z, c.w};
   unsigned hit[4];
 #pragma unroll
   for (int r = 0; r < 4; ++r) hit[r] = frontier_bit(sm, sbits, gbm, cc[r]);
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    first[r] = (hit[r] && first[r] < 0) ? cc[r] : first[r];
-    if (SR == SS_REAL && hit[r] && (live >> r & 1u)) sum[r] += __ldg(d.fr + cc[r]);
+  for (int r = 0; r < 4; ++r) first[r] = (hit[r] && first[r] < 0) ? cc[r] : first[r];
+  if (SR == SS_REAL) {
+    const unsigned m = (hit[0] | (hit[1] << 1) | (hit[2] << 2) | (hit[3] << 3)) & live;
+    if (m) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        if (m >> r & 1u) sum[r] += (cc[r] < sf) ? smf[cc[r]] : __ldg(d.fr + cc[r]);
+    }
   }
 }
 
@@ -270,7 +288,14 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_pull(Dev d, int variant,
   const int pv = d.ctl->prev_variant;
   const bool light = (pv == VAR_FULL || pv == VAR_SLIMWORK || pv == VAR_FILTERED) &&
                      d.ctl->prev_slots < STAGE_MIN_SLOTS;
-  const int sw = light ? 0 : d.smem_words;
+  const int sw_all = light ? 0 : d.smem_words;
+  // real semiring on a level whose frontier carries a large share of the edges
+  // (the hub level of a skewed graph): the last sf words of the staging area
+  // hold the values fr of the sf highest-degree rows instead of bitmap words
+  const bool hub = SR == SS_REAL && (unsigned long long)d.ctl->prev_deg * HUB_EDGE_SHARE >
+                                        (unsigned long long)d.nnz;
+  const int sf = hub ? min(HUB_VALUE_ROWS, (sw_all >> 1) & ~3) : 0;
+  const int sw = sw_all - sf;  // bitmap words staged (a multiple of 4)
   {
     if (threadIdx.x < SMEM_GUARD) ss_smem_bits[threadIdx.x] = 0u;
     const unsigned sbase = (unsigned)__cvta_generic_to_shared(ss_smem_bits + SMEM_GUARD);
@@ -278,10 +303,16 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_pull(Dev d, int variant,
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sbase + 16u * (unsigned)i),
                    "l"(reinterpret_cast<const int4*>(gbm) + i)
                    : "memory");
+    const unsigned fbase = sbase + 4u * (unsigned)sw;
+    for (int i = threadIdx.x; i < (sf >> 2); i += PULL_THREADS)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(fbase + 16u * (unsigned)i),
+                   "l"(reinterpret_cast<const int4*>(d.fr) + i)
+                   : "memory");
     asm volatile("cp.async.wait_all;\n" ::: "memory");
   }
   __syncthreads();
   const unsigned* sm = ss_smem_bits + SMEM_GUARD;
+  const float* smf = reinterpret_cast<const float*>(sm + sw);
   const int sbits = sw * 32;
   Counters cnt;
   unsigned long long lane_slots = 0;
@@ -342,7 +373,7 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_pull(Dev d, int variant,
         c[u] = (u < ncols) ? ld_stream(base + u * Q) : make_int4(-1, -1, -1, -1);
 #pragma unroll
       for (int u = 0; u < SHORT_COLS; ++u)
-        if (u < ncols) scan_quad<SR>(d, sm, sbits, gbm, c[u], first, sum, live);
+        if (u < ncols) scan_quad<SR>(d, sm, sbits, gbm, c[u], first, sum, live, smf, sf);
       if (own && lq == 0) {
         cnt.act += 1;
         if (MODE != MODE_FILTERED) cnt.slots += (unsigned long long)ncols * C;
@@ -412,7 +443,7 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_pull(Dev d, int variant,
         }
 #pragma unroll
         for (int u = 0; u < PULL_STEP; ++u)
-          if (q0 + 32 * u < nq) scan_quad<SR>(d, sm, sbits, gbm, c[u], first, sum, live);  // warp-uniform
+          if (q0 + 32 * u < nq) scan_quad<SR>(d, sm, sbits, gbm, c[u], first, sum, live, smf, sf);  // warp-uniform
         if (MODE == MODE_FILTERED) {  // a row is done once visited or (not real) hit
           need = false;
 #pragma unroll
@@ -880,6 +911,46 @@ ss_status slimsell_bfs(slimsell_handle h, int32_t root, int32_t semiring, int32_
     ss_status s = loop_graph(h, d, semiring, policy, &exec);
     if (s != SS_OK) return s;
     SS_CUDA(cudaGraphLaunch(exec, st));
+  } else if (!adaptive(policy) && h->profile_queue) {
+    // fixed variant: iterations are queued QUEUE_BATCH at a time, each launch
+    // bracketed by its own event pair when profiling, and the host reads the
+    // counter once per batch; launches queued past the end of the run return
+    // at once (every kernel checks the done flag) and their times are dropped
+    constexpr int QUEUE_BATCH = 8;
+    if (prof && h->evq.size() < 2 * (size_t)QUEUE_BATCH) {
+      while (h->evq.size() < 2 * (size_t)QUEUE_BATCH) {
+        cudaEvent_t e = nullptr;
+        SS_CUDA(cudaEventCreate(&e));
+        h->evq.push_back(e);
+      }
+    }
+    const long long max_iter = (long long)h->n + 2;
+    for (long long it = 0;;) {
+      if (it > max_iter) {
+        set_error("slimsell_bfs: no convergence after %lld iterations", it);
+        return SS_ERR_CUDA;
+      }
+      for (int j = 0; j < QUEUE_BATCH; ++j) {
+        ss_status s = launch_decide(h, d, policy, 0, 0, st);  // logs the iteration's features
+        if (s != SS_OK) return s;
+        if (prof) SS_CUDA(cudaEventRecord(h->evq[2 * j], st));
+        s = launch_variant(h, d, semiring, policy, IterLaunch{policy, 0, 0}, st);
+        if (s != SS_OK) return s;
+        if (prof) SS_CUDA(cudaEventRecord(h->evq[2 * j + 1], st));
+      }
+      SS_CUDA(cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+      SS_CUDA(cudaStreamSynchronize(st));
+      const long long ran = (long long)h->h_ctl->k - 1;  // iterations the run has made so far
+      if (prof)
+        for (int j = 0; j < QUEUE_BATCH && it + j < ran; ++j) {
+          float ms = 0.f;
+          SS_CUDA(cudaEventElapsedTime(&ms, h->evq[2 * j], h->evq[2 * j + 1]));
+          iter_ms += ms;
+          h->iter_ns.push_back((int)(ms * 1.0e6f));
+        }
+      it += QUEUE_BATCH;
+      if (h->h_ctl->done) break;
+    }
   } else {
     const long long max_iter = (long long)h->n + 2;
     for (long long it = 0;; ++it) {
@@ -986,6 +1057,9 @@ ss_status slimsell_set_option(slimsell_handle h, int32_t option, int64_t value) 
       return SS_OK;
     case SS_OPT_DEVICE_LOOP:
       h->device_loop = value ? 1 : 0;
+      return SS_OK;
+    case SS_OPT_PROFILE_QUEUE:
+      h->profile_queue = value ? 1 : 0;
       return SS_OK;
     case SS_OPT_SELECTOR_MARGIN:
       if (value < 0 || value > 100000) {

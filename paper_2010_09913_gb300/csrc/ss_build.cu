@@ -603,6 +603,7 @@ void free_handle(slimsell_graph* h) {
   if (h->ev_b) cudaEventDestroy(h->ev_b);
   if (h->ev_c) cudaEventDestroy(h->ev_c);
   if (h->ev_d) cudaEventDestroy(h->ev_d);
+  for (cudaEvent_t e : h->evq) cudaEventDestroy(e);
   if (h->ev_done) {
     cudaEventSynchronize(h->ev_done);
     cudaEventDestroy(h->ev_done);

@@ -192,9 +192,11 @@ struct slimsell_graph {
   cudaEvent_t ev_done = nullptr;       // end of the last call's work on its stream
   int pending = 0;                     // last-run statistics not yet read back
   int device_loop = 1;                 // iterate with a conditional CUDA graph
+  int profile_queue = 1;               // host-driven fixed variants: queue iterations in batches
   cudaGraphExec_t loop_exec[4][6] = {};  // [semiring][policy] device-side iteration loops
   int loop_smem_words[4][6] = {};
   std::vector<int> iter_ns;            // per-iteration kernel time of the last profiled call
+  std::vector<cudaEvent_t> evq;        // event pairs of a queued host-driven batch of iterations
 
   ss::Dev dev() const;
 };

@@ -54,7 +54,7 @@ __global__ void k_decide(Dev d, int policy, cudaGraphConditionalHandle sw, int u
   Ctl* c = d.ctl;
   const int t = threadIdx.x;
   if (t == 0) {
-    stop = 0;
+    stop = c->done;  // host-driven queued loops launch past the end of a run
     if (use_cw) {
       c->loop_guard += 1;
       if (c->done || c->loop_guard > (unsigned long long)d.n + 2) {

@@ -23,21 +23,27 @@ import math
 import numpy as np
 import torch
 
-from . import (N_OUTPUTS, N_PARAMS, slimsell_get_features, slimsell_mlp_train_step,
-               slimsell_selector_load, slimsell_set_profiling)
+from . import (N_OUTPUTS, N_PARAMS, OPT_PROFILE_QUEUE, slimsell_get_features,
+               slimsell_mlp_train_step, slimsell_selector_load, slimsell_set_option,
+               slimsell_set_profiling)
 
 VARIANTS = ["full", "slimwork", "push", "pull_filtered"]
 
 
 def _profiled_run(G, root: int, semiring: str, policy: str):
-    """One BFS with per-iteration kernel times; returns (ns[k], variant[k], features[k])."""
+    """One BFS with per-iteration kernel times; returns (ns[k], variant[k], features[k]).
+    Every variant is timed the same way, one launch and one counter read per
+    iteration (the adaptive push cannot be queued ahead), so that the labels
+    compare like with like."""
     slimsell_set_profiling(G.h, True)
+    slimsell_set_option(G.h, OPT_PROFILE_QUEUE, 0)
     G.bfs(int(root), semiring, policy, want_parent=False)
     st, its = G.run_stats(cap=65536)
     iters = st.iterations
     ns = np.array([its[k].kernel_ns for k in range(1, iters + 1)], dtype=np.float64)
     var = np.array([its[k].variant for k in range(1, iters + 1)], dtype=np.int32)
     feats = slimsell_get_features(G.h, iters + 1)[1:iters + 1]
+    slimsell_set_option(G.h, OPT_PROFILE_QUEUE, 1)
     slimsell_set_profiling(G.h, False)
     return ns, var, feats
 

@@ -126,7 +126,8 @@ def test_options_do_not_change_results(smem, dp_pass):
 
 
 def test_device_loop_matches_host_loop():
-    """The conditional-graph iteration loop and the host-driven loop agree exactly."""
+    """The conditional-graph iteration loop and the host-driven loop (queued in
+    batches, and one iteration at a time) agree exactly."""
     g = gg.kronecker(12, seed=4)
     G = ss.SlimSellGraph.from_host(g.row_ptr, g.col, C=32, sigma=g.n, split_w=32)
     for r in gg.roots(g, 3, seed=7):
@@ -134,15 +135,40 @@ def test_device_loop_matches_host_loop():
         for sr in SEMIRINGS:
             for pol in ("full", "slimwork", "pull_filtered", "push", "heuristic"):
                 res = []
-                for loop in (1, 0):
+                for loop, queue in ((1, 1), (0, 1), (0, 0)):
                     G.set_option(ss.OPT_DEVICE_LOOP, loop)
+                    G.set_option(ss.OPT_PROFILE_QUEUE, queue)
                     dist, parent = run(G, r, sr, pol)
                     np.testing.assert_array_equal(dist, d)
                     np.testing.assert_array_equal(parent, p)
                     st, iters = G.run_stats(cap=64)
                     res.append((st.iterations, st.reached, st.slots,
                                 [(iters[i].frontier, iters[i].slots) for i in range(st.iterations + 1)]))
-                assert res[0] == res[1]
+                assert res[0] == res[1] == res[2]
+    G.close()
+
+
+@pytest.mark.parametrize("queue", [1, 0])
+def test_profiled_loop_times_every_iteration(queue):
+    """Profiling with a fixed variant: every iteration of a long run (a 70-vertex
+    path: 70 passes, so the queued loop ends inside its ninth batch of eight)
+    gets a kernel time, and the results equal the oracle's."""
+    g = gg.from_edges(70, [(i, i + 1) for i in range(69)])
+    G = ss.SlimSellGraph.from_host(g.row_ptr, g.col, C=8, sigma=g.n, split_w=2)
+    G.set_option(ss.OPT_PROFILE_QUEUE, queue)
+    ss.slimsell_set_profiling(G.h, True)
+    for sr in SEMIRINGS:
+        for pol in ("full", "slimwork", "pull_filtered"):
+            d, p = expected(g, 0)
+            dist, parent = run(G, 0, sr, pol)
+            np.testing.assert_array_equal(dist, d)
+            np.testing.assert_array_equal(parent, p)
+            st, iters = G.run_stats(cap=80)
+            assert st.iterations == 70
+            ns = [iters[i].kernel_ns for i in range(1, st.iterations + 1)]
+            assert all(x > 0 for x in ns), (sr, pol, ns)
+            assert st.iter_kernel_ms > 0
+    ss.slimsell_set_profiling(G.h, False)
     G.close()
 
 
