@@ -65,7 +65,8 @@ typedef enum {
                              (SS_VARIANT_PUSH_LOCAL)                                           */
   SS_V_PULL_FILTERED = 3, /* pull over unvisited rows only, stopping at the first hit         */
   SS_V_HEURISTIC = 4,     /* per-iteration choice by a frontier-size rule                      */
-  SS_V_LEARNED = 5        /* per-iteration choice by the loaded selector MLP                   */
+  SS_V_LEARNED = 5        /* per-iteration choice by the loaded selector MLP; frontiers the
+                             cluster push takes go to it, as in SS_V_HEURISTIC                 */
 } ss_policy;
 
 /* Executed-variant id (ss_iter_stats.variant, not a policy) of the cluster
@@ -271,6 +272,71 @@ ss_status slimsell_batch_run(slimsell_batch_handle b, const int32_t* d_roots,
                              int32_t* const* h_dist, int32_t* const* h_parent, void* stream);
 ss_status slimsell_batch_get_stats(slimsell_batch_handle b, ss_run_stats* out);
 void slimsell_batch_destroy(slimsell_batch_handle b);
+
+/*
+ * Layout autotuner (an extension; the paper tunes C, sigma and the SlimChunk
+ * split by hand, Sections III-D and IV).  For every point of the grid
+ * C x sigma x split_w it builds the layout (slimsell_build), runs one untimed
+ * BFS from h_roots[0] (which builds the handle's device-side loop), then times
+ * `repeats` passes over all roots with CUDA events on `stream`, and keeps the
+ * point with the smallest mean time per BFS (no outputs written: dist and
+ * parent NULL).
+ *   d_row_ptr, d_col, n, nnz  the graph, as for slimsell_build (device).
+ *   semiring, policy          as for slimsell_bfs.
+ *   h_roots[nroots]           host, each in [0, n).
+ *   h_C[nC]                   host, each 8, 16, 32 or 64.
+ *   h_sigma[nsigma]           host, each >= 0; 0 means n (a global sort).
+ *   h_split_w[nw]             host, each >= 0 (0 = no splitting).
+ *   use_cache                 1: a graph whose signature matches a cached search
+ *                             (slimsell_tune_match) with the same semiring,
+ *                             policy and grid reuses it without timing.
+ *   h_result                  host: the best point, the number of points timed
+ *                             (0 when cached) and whether the cache answered.
+ *   h_table[table_cap]        host or NULL: every grid point and its time, C
+ *                             slowest-varying, then sigma, then split_w.
+ * Every search is added to a process-wide cache (guarded by a mutex).  The call
+ * synchronises `stream`.  Errors: SS_ERR_INVALID (NULL pointers, empty grids or
+ * roots, a root, C, sigma or split_w out of range), SS_ERR_OOM, SS_ERR_CUDA.
+ */
+typedef struct {
+  int32_t C;        /* chunk height                                            */
+  int32_t sigma;    /* sorting scope as in the grid (0 = n)                     */
+  int32_t split_w;  /* SlimChunk split width                                    */
+  float ms;         /* mean time of one BFS in milliseconds                     */
+} ss_tune_point;
+
+typedef struct {
+  ss_tune_point best;
+  int32_t points;   /* grid points timed by this call (0 if the cache answered) */
+  int32_t cached;   /* 1 if a cached search of a matching graph was reused      */
+} ss_tune_result;
+
+/* Cache key of a graph: n, nnz rounded to two significant digits, and
+ * hist[b] = 50 x (vertices with floor(log2 degree) = b) / n, rounded to the
+ * nearest integer, for b = 0 .. 23 (isolated vertices are not counted). */
+typedef struct {
+  int32_t n;
+  int64_t nnz_rounded;
+  int32_t hist[24];
+} ss_tune_signature;
+
+ss_status slimsell_autotune(const int64_t* d_row_ptr, const int32_t* d_col, int32_t n, int64_t nnz,
+                            int32_t semiring, int32_t policy, const int32_t* h_roots, int32_t nroots,
+                            const int32_t* h_C, int32_t nC, const int32_t* h_sigma, int32_t nsigma,
+                            const int32_t* h_split_w, int32_t nw, int32_t repeats, int32_t use_cache,
+                            ss_tune_result* h_result, ss_tune_point* h_table, int32_t table_cap,
+                            void* stream);
+
+/* Signature of a graph from its HOST row offsets h_row_ptr[n + 1] (host-only
+ * computation, the same one slimsell_autotune makes on the device).
+ * Errors: SS_ERR_INVALID (NULL pointers, n < 0). */
+ss_status slimsell_tune_signature(const int64_t* h_row_ptr, int32_t n, ss_tune_signature* out);
+
+/* 1 if two signatures would share a cached search: equal n and rounded nnz and
+ * histograms within 3 units in L1 distance (so graphs of one family and size
+ * share a search even where two seeds' shares fall on opposite sides of a
+ * rounding edge); 0 otherwise (also for NULL arguments). */
+int32_t slimsell_tune_match(const ss_tune_signature* a, const ss_tune_signature* b);
 
 /* Layout summary. */
 ss_status slimsell_get_info(slimsell_handle h, ss_info* out);

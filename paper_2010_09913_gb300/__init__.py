@@ -54,6 +54,19 @@ class ss_run_stats(ctypes.Structure):
                 ("iter_kernel_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
 
 
+class ss_tune_point(ctypes.Structure):
+    _fields_ = [("C", ctypes.c_int32), ("sigma", ctypes.c_int32), ("split_w", ctypes.c_int32),
+                ("ms", ctypes.c_float)]
+
+
+class ss_tune_result(ctypes.Structure):
+    _fields_ = [("best", ss_tune_point), ("points", ctypes.c_int32), ("cached", ctypes.c_int32)]
+
+
+class ss_tune_signature(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz_rounded", ctypes.c_int64), ("hist", ctypes.c_int32 * 24)]
+
+
 _lib = None
 _VP = ctypes.c_void_p
 
@@ -91,6 +104,10 @@ def lib():
         "slimsell_batch_run": (i32, [_VP, _VP, _VP, _VP, _VP]),
         "slimsell_batch_get_stats": (i32, [_VP, ctypes.POINTER(ss_run_stats)]),
         "slimsell_batch_destroy": (None, [_VP]),
+        "slimsell_autotune": (i32, [_VP, _VP, i32, i64, i32, i32, _VP, i32, _VP, i32, _VP, i32, _VP, i32,
+                                    i32, i32, ctypes.POINTER(ss_tune_result), _VP, i32, _VP]),
+        "slimsell_tune_signature": (i32, [_VP, i32, ctypes.POINTER(ss_tune_signature)]),
+        "slimsell_tune_match": (i32, [ctypes.POINTER(ss_tune_signature), ctypes.POINTER(ss_tune_signature)]),
         "slimsell_last_error": (ctypes.c_char_p, []),
         "slimsell_version": (ctypes.c_char_p, []),
     }
@@ -111,6 +128,7 @@ def exported_symbols() -> list[str]:
             "slimsell_sigma_sort_noalloc", "slimsell_selector_load", "slimsell_get_features",
             "slimsell_mlp_forward", "slimsell_mlp_train_step", "slimsell_batch_create",
             "slimsell_batch_run", "slimsell_batch_get_stats", "slimsell_batch_destroy",
+            "slimsell_autotune", "slimsell_tune_signature", "slimsell_tune_match",
             "slimsell_last_error", "slimsell_version"]
 
 
@@ -259,6 +277,41 @@ def slimsell_mlp_train_step(w, m, v, step, x, t, mask, lr, grad=None, loss=None,
         _ptr(x, torch.float32, "x"), _ptr(t, torch.float32, "t"), _ptr(mask, torch.float32, "mask"),
         int(x.shape[0]), float(lr), _ptr(grad, torch.float32, "grad") if grad is not None else None,
         _ptr(loss, torch.float32, "loss") if loss is not None else None, _stream(stream)))
+
+
+def slimsell_autotune(row_ptr: torch.Tensor, col: torch.Tensor, n: int, nnz: int, semiring: int,
+                      policy: int, roots, Cs, sigmas, split_ws, repeats: int = 2, use_cache: bool = True,
+                      stream=None):
+    """Layout autotuner; returns (ss_tune_result, [ss_tune_point, ...] in grid order)."""
+    import numpy as np
+    r = np.ascontiguousarray(np.asarray(roots, dtype=np.int32))
+    gc = np.ascontiguousarray(np.asarray(Cs, dtype=np.int32))
+    gs = np.ascontiguousarray(np.asarray(sigmas, dtype=np.int32))
+    gw = np.ascontiguousarray(np.asarray(split_ws, dtype=np.int32))
+    total = gc.size * gs.size * gw.size
+    table = (ss_tune_point * total)()
+    res = ss_tune_result()
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    _check("slimsell_autotune", lib().slimsell_autotune(
+        _ptr(row_ptr, torch.int64, "row_ptr"), _ptr(col, torch.int32, "col"), int(n), int(nnz),
+        int(semiring), int(policy), p(r), int(r.size), p(gc), int(gc.size), p(gs), int(gs.size),
+        p(gw), int(gw.size), int(repeats), 1 if use_cache else 0, ctypes.byref(res), table, total,
+        _stream(stream)))
+    return res, list(table)
+
+
+def slimsell_tune_signature(row_ptr) -> ss_tune_signature:
+    """Cache key of a graph from host row offsets (numpy int64)."""
+    import numpy as np
+    rp = np.ascontiguousarray(np.asarray(row_ptr, dtype=np.int64))
+    out = ss_tune_signature()
+    _check("slimsell_tune_signature", lib().slimsell_tune_signature(
+        rp.ctypes.data_as(ctypes.c_void_p), int(rp.size - 1), ctypes.byref(out)))
+    return out
+
+
+def slimsell_tune_match(a: ss_tune_signature, b: ss_tune_signature) -> bool:
+    return bool(lib().slimsell_tune_match(ctypes.byref(a), ctypes.byref(b)))
 
 
 def slimsell_batch_create(handles, semiring: int, policy: int) -> int:

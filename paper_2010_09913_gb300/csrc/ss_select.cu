@@ -7,7 +7,8 @@
 // frontier size (top-down while the frontier's edges are few compared with
 // the unexplored ones); the learned policy evaluates a 16-64-64-4 MLP on the
 // iteration's features and takes the variant with the smallest predicted
-// log-time.  Schedules never change results, only their cost.
+// log-time, except for frontiers small enough for the cluster push, which both
+// adaptive policies hand to it.  Schedules never change results, only their cost.
 //
 // MLP parameters (fp32, 5508 values, inputs first):
 //   W1[16][64] | b1[64] | W2[64][64] | b2[64] | W3[64][4] | b3[4]
@@ -113,6 +114,10 @@ __global__ void k_decide(Dev d, int policy, cudaGraphConditionalHandle sw, int u
       int hv = choice;
       if (hv == VAR_PUSH && !push_fits(d, c)) hv = VAR_FILTERED;
       if (d.sel_margin > 0.0f && y[best] + d.sel_margin >= y[hv]) best = hv;
+      // a frontier the cluster push takes stays with it: that launch runs the
+      // following small levels too, a saving no per-level time can express, so
+      // the network only chooses among levels that need a grid-wide pass
+      if (local_fits(d, c->prev_new, c->prev_deg)) best = VAR_PUSH;
       choice = best;
     }
     __syncthreads();

@@ -137,3 +137,28 @@ def evaluate(G, roots, semiring: str = "tropical", weights=None, repeats: int = 
             out[pol] += np.median([_profiled_run(G, int(r), semiring, pol)[0].sum()
                                    for _ in range(repeats)]) / 1e6
     return out
+
+
+def device_times(G, roots, semiring: str, policies, reps: int = 15):
+    """Whole-run device time (ms, summed over roots) of each policy with the
+    device-side loop: CUDA events around every run, the median of `reps` runs
+    per root (one warm-up run per policy first)."""
+    from . import POLICIES, SEMIRINGS, slimsell_bfs
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    out = {}
+    for pol in policies:
+        slimsell_bfs(G.h, int(roots[0]), SEMIRINGS[semiring], POLICIES[pol], None, None, stream)
+        total = 0.0
+        for r in roots:
+            ts = []
+            for _ in range(reps):
+                e0.record(stream)
+                slimsell_bfs(G.h, int(r), SEMIRINGS[semiring], POLICIES[pol], None, None, stream)
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            total += float(np.median(ts))
+        out[pol] = total
+    return out

@@ -62,11 +62,43 @@ def test_batch_invalid():
 
 
 def test_autotune_returns_grid_point_and_caches():
+    """slimsell_autotune through the C ABI: every grid point timed once, the best
+    point's layout gives the oracle's BFS, and graphs with a matching signature
+    (same family and size, same grid) are answered from the cache."""
     g = gg.kronecker(11, seed=4)
     roots = gg.roots(g, 2, seed=1)
-    grid = {"C": (16, 32), "sigma": (1, "n"), "split_w": (256, 4096)}
-    best, table = autotune.tune(g.row_ptr, g.col, roots, grid=grid, repeats=1)
-    assert len(table) == 8 and best in [p for p, _ in table]
-    assert best["C"] in grid["C"] and best["sigma"] in grid["sigma"]
-    again, _ = autotune.tune(g.row_ptr, g.col, roots, grid=grid)
-    assert again == best
+    grid = {"C": (16, 32), "sigma": (1, 256, "n"), "split_w": (256, 4096)}
+    best, table, res = autotune.tune(g.row_ptr, g.col, roots, grid=grid, repeats=1, use_cache=False,
+                                     with_result=True)
+    assert res.cached == 0 and res.points == 12 and len(table) == 12
+    assert [p for p, _ in table][:3] == [{"C": 16, "sigma": 1, "split_w": 256},
+                                         {"C": 16, "sigma": 1, "split_w": 4096},
+                                         {"C": 16, "sigma": 256, "split_w": 256}]
+    assert all(ms > 0 for _, ms in table)
+    assert best == min(table, key=lambda t: t[1])[0]
+    G = ss.SlimSellGraph.from_host(g.row_ptr, g.col, C=best["C"],
+                                   sigma=g.n if best["sigma"] == "n" else best["sigma"],
+                                   split_w=best["split_w"])
+    r = int(roots[0])
+    d = oracle.bfs_queue(g.row_ptr, g.col, r)
+    dist, parent = G.bfs(r, "tropical", "slimwork")
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(dist.cpu().numpy(), d)
+    np.testing.assert_array_equal(parent.cpu().numpy(), oracle.dp(g.row_ptr, g.col, d, r))
+    G.close()
+    again, table2, res2 = autotune.tune(g.row_ptr, g.col, roots, grid=grid, with_result=True)
+    assert res2.cached == 1 and res2.points == 0 and again == best and table2 == table
+    other, _, res3 = autotune.tune(gg.kronecker(11, seed=5).row_ptr, gg.kronecker(11, seed=5).col,
+                                   roots, grid=grid, with_result=True)
+    assert res3.cached == 1 and other == best  # same family and size
+    _, _, res4 = autotune.tune(g.row_ptr, g.col, roots, grid=grid, semiring="real", repeats=1,
+                               with_result=True)
+    assert res4.cached == 0 and res4.points == 12  # another semiring searches again
+
+
+def test_autotune_rejects_bad_grids():
+    g = gg.kronecker(8, seed=1)
+    with pytest.raises(ss.SlimSellError):
+        autotune.tune(g.row_ptr, g.col, [0], grid={"C": (12,), "sigma": (1,), "split_w": (0,)})
+    with pytest.raises(ss.SlimSellError):
+        autotune.tune(g.row_ptr, g.col, [g.n], grid={"C": (8,), "sigma": (1,), "split_w": (0,)})

@@ -152,7 +152,7 @@ def test_training_reduces_loss():
 def test_selector_training_pipeline():
     """Collect per-iteration variant timings, train the MLP on the GPU, and check what it
     learned: its argmin matches the measured-fastest variant on most iterations, and the
-    learned schedule costs no more than the slower fixed schedules."""
+    learned schedule beats plain SlimWork and keeps up with the frontier-size rule."""
     from paper_2010_09913_gb300 import selector
 
     graphs = [gg.kronecker(15, seed=3), gg.lattice(96, 0.05, seed=2)]
@@ -173,11 +173,21 @@ def test_selector_training_pipeline():
     # near-ties (within 10%) count as a match
     close = T[np.arange(len(pred)), pred] <= T[np.arange(len(best)), best] + np.log(1.10)
     assert close.mean() >= 0.6, close.mean()
-    G, g = handles[0]
-    res = selector.evaluate(G, gg.roots(g, 2, seed=4), "tropical", weights=w, repeats=2)
-    worst_fixed = max(res[v] for v in selector.VARIANTS)
-    assert res["learned"] <= worst_fixed, res
-    for G, _ in handles:
+    # what the trained network gains, timed as the library runs it (device-side
+    # loop, median of 15 runs per root) on every training family: less time than
+    # the plain SlimWork pass by a stated factor (5 % on the small Kronecker graph,
+    # where the frontier-size rule itself gains about 15 %; half on the lattice,
+    # whose small levels go to the cluster push), and within 5 % of the rule (the
+    # rule is also its fallback, with the bench's margin of 0.1)
+    gain = [0.95, 0.5]
+    for (G, g), factor in zip(handles, gain):
+        ss.slimsell_selector_load(G.h, w)
+        G.set_option(ss.OPT_SELECTOR_MARGIN, 100)
+        t = selector.device_times(G, gg.roots(g, 2, seed=4), "tropical",
+                                  ["slimwork", "heuristic", "learned"])
+        assert t["learned"] <= factor * t["slimwork"], (g.name, t)
+        assert t["learned"] <= 1.05 * t["heuristic"], (g.name, t)
+        ss.slimsell_selector_load(G.h, None)
         G.close()
 
 
