@@ -185,9 +185,14 @@ ss_status slimsell_bfs_multi(slimsell_handle h, const int32_t* d_roots, int32_t 
  *            the largest-id neighbour of v one level closer to roots[s]
  *            (roots[s] for the root itself, -1 if unreached): for every source,
  *            the canonical parent that slimsell_bfs returns for that root.
- * Parents are found by a pass after each level: neighbours are stored in
- * descending original id, so for each source a vertex gained, the first
- * neighbour that was in that source's previous frontier is its parent.
+ * Parents are found by a pass after each level, in one of two directions
+ * chosen per level from the previous level's counters: while the run grows and
+ * the previous frontier's rows carry at most half of the edges, a push from
+ * that frontier (each frontier row u offers itself to its neighbours that
+ * gained a source u's frontier holds; atomicMax keeps the largest id);
+ * otherwise a walk from the gaining rows (neighbours are stored in descending
+ * original id, so for each source a vertex gained, the first neighbour that was
+ * in that source's previous frontier is its parent).
  * slimsell_bfs_multi is this call with d_parent = NULL.
  * Errors: as slimsell_bfs_multi.
  */

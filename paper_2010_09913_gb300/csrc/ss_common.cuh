@@ -70,6 +70,9 @@ struct Ctl {
   unsigned long long qlen[2];     // vertex-list lengths, by level parity
   unsigned long long qprep;       // length of a list just built from the bitmap
   unsigned long long loop_guard;  // decide-kernel executions in this run (device loop bound)
+  unsigned long long new_rowdeg;  // multi-source: degree sum of the rows that gained a source
+                                  // in the current iteration (each row counted once)
+  unsigned long long prev_rowdeg; // ... in the previous iteration
 };
 
 // Flat view of the handle's device buffers handed to kernels by value.

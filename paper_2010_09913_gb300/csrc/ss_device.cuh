@@ -16,6 +16,33 @@ __device__ __forceinline__ bool local_fits(const Dev& d, unsigned long long nf, 
   return nf <= (unsigned long long)d.local_max_nf && mf <= (unsigned long long)d.local_max_e;
 }
 
+// Neighbours per push work unit: a frontier row of degree D becomes ceil(D / PUSH_UNIT)
+// units (row, first neighbour index), so hub rows spread over many warps.
+constexpr int PUSH_UNIT = 256;
+
+// Emit the work units of frontier vertex u (deg > 0), warp-aggregated.  All
+// lanes of the warp call; lanes with u < 0 emit nothing.
+__device__ __forceinline__ void emit_units(const Dev& d, int u, int lane) {
+  const int deg = (u >= 0) ? d.rdeg[u] : 0;
+  const unsigned nu = (unsigned)((deg + PUSH_UNIT - 1) / PUSH_UNIT);
+  unsigned incl = nu;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned t = __shfl_up_sync(SS_FULL_MASK, incl, o);
+    if (lane >= o) incl += t;
+  }
+  const unsigned total = __shfl_sync(SS_FULL_MASK, incl, 31);
+  unsigned long long base = 0;
+  if (lane == 31 && total) base = atomicAdd(&d.ctl->units, (unsigned long long)total);
+  base = __shfl_sync(SS_FULL_MASK, base, 31);
+  const unsigned long long first = base + incl - nu;
+  if (first + nu > (unsigned long long)d.units_cap) {  // cannot happen after the decide check
+    if (nu) atomicOr(&d.ctl->error, 2);
+    return;
+  }
+  for (unsigned q = 0; q < nu; ++q) d.units[first + q] = make_int2(u, (int)(q * PUSH_UNIT));
+}
+
 struct IterLaunch {
   int variant;
   cudaGraphConditionalHandle cond;  // WHILE-loop condition of the device-side loop
@@ -78,6 +105,8 @@ __device__ __forceinline__ void iteration_tail(const Dev& d, int variant,
   const unsigned long long ac = atomicAdd(&c->active, 0ull);
   const unsigned md = atomicMax(&c->new_maxdeg, 0u);
   const bool stop = advance_level(d, c, k, nc, nd, sl, ac, md, variant);
+  c->prev_rowdeg = c->new_rowdeg;
+  c->new_rowdeg = 0;
   c->list_level = -1;
   c->new_count = 0;
   c->new_deg = 0;

@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(C * W) k_multi_pull(MultiDev m, IterLaunch il)
   unsigned* FAn = d.fb[level & 1];
   __shared__ int s_flag;
   __shared__ unsigned s_fa[2];
-  unsigned long long nw = 0, deg = 0, slots = 0, act = 0;
+  unsigned long long nw = 0, deg = 0, slots = 0, act = 0, rowdeg = 0;
   unsigned maxdeg = 0;
   for (int it = blockIdx.x; it < d.n_items; it += gridDim.x) {
     const int4 item = d.items[it];
@@ -182,11 +182,20 @@ __global__ void __launch_bounds__(C * W) k_multi_pull(MultiDev m, IterLaunch il)
     }
     Fn[row * W + w] = nb;
     const int left = __syncthreads_or((vold | nb) != ~0ull);
+    if (w == 0 && ((s_fa[r >> 5] >> (r & 31)) & 1u)) rowdeg += (unsigned long long)d.rdeg[row];
     if (tid == 0) {
       store_summary<C>(FAn, chunk, s_fa[0], s_fa[1]);
       d.act[chunk] = left ? 1 : 3;
       act += 1;
     }
+  }
+  // degree sum of the rows that gained a source, each row counted once (the
+  // parents pass picks its direction from it)
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) rowdeg += __shfl_down_sync(SS_FULL_MASK, rowdeg, off);
+  if ((tid & 31) == 0 && rowdeg) {
+    atomicAdd(&c->new_rowdeg, rowdeg);
+    __threadfence();  // before this block counts itself done
   }
   finish_iteration_block<T>(d, nw, deg, slots, act, maxdeg, il);
 }
@@ -245,6 +254,8 @@ __global__ void k_multi_roots(MultiDev m, int W, int* parent) {
     c->loop_guard = 0;
     for (int v = 0; v < N_VARIANTS; ++v) c->variant_count[v] = 0;
     c->list_level = -1; c->list_prev_ok = 0; c->qlen[0] = c->qlen[1] = 0; c->qprep = 0;
+    c->new_rowdeg = 0;
+    c->prev_rowdeg = rd;  // the roots' rows (a repeated root counted again: an upper bound)
     ss_iter_stats st;
     st.frontier = m.k; st.frontier_degree = (long long)rd; st.slots = 0; st.active_chunks = 0;
     st.variant = -1; st.kernel_ns = 0;
@@ -260,6 +271,12 @@ __global__ void k_multi_roots(MultiDev m, int W, int* parent) {
 // by the whole warp, 32 neighbours per step, the candidates taken in lane
 // (= storage) order.  Plain stores: one lane owns each (row, word) entry.
 constexpr int MULTI_PAR_SHORT = 32;
+// The parents pass pushes from the previous frontier while the run grows and
+// that frontier's rows carry at most nnz / MULTI_PAR_PUSH_SHARE edges.
+#ifndef SS_MULTI_PAR_PUSH_SHARE
+#define SS_MULTI_PAR_PUSH_SHARE 2
+#endif
+constexpr unsigned long long MULTI_PAR_PUSH_SHARE = SS_MULTI_PAR_PUSH_SHARE;
 
 __global__ void __launch_bounds__(256) k_multi_parents(MultiDev m, int W, int lgW, int level, int* parent) {
   const Dev& d = m.d;
@@ -332,6 +349,69 @@ __global__ void __launch_bounds__(256) k_multi_parents(MultiDev m, int W, int lg
               b &= b - 1;
             }
           }
+        }
+      }
+    }
+  }
+}
+
+// Parents of the sources gained at `level`, pushed from the frontier of level
+// - 1 (for levels whose frontier rows carry few edges).  k_multi_par_expand
+// turns every row u of that frontier (summary bit set) into units of
+// PUSH_UNIT neighbours; in k_multi_par_scatter one warp takes a unit and its
+// lanes walk the unit's neighbours v: each source s in F[level][v] &
+// F[level-1][u] has u one level closer to s than v, and atomicMax keeps the
+// largest original id over all such u (parents start at -1).
+__global__ void __launch_bounds__(256) k_multi_par_expand(MultiDev m, int level) {
+  const Dev& d = m.d;
+  const unsigned* FAp = d.fb[(level - 1) & 1];
+  const int lane = threadIdx.x & 31;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long words = ((long long)d.n_pad + 31) / 32;
+  const long long wstride = stride & ~31LL;  // whole warps walk the summary together
+  for (long long i0 = t0 - lane; i0 < words; i0 += wstride) {
+    const long long i = i0 + lane;
+    unsigned bits = i < words ? FAp[i] : 0u;
+    while (__any_sync(SS_FULL_MASK, bits != 0u)) {
+      int u = -1;
+      if (bits) {
+        const int b = __ffs(bits) - 1;
+        bits &= bits - 1;
+        u = (int)(i * 32 + b);
+      }
+      emit_units(d, u, lane);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_multi_par_scatter(MultiDev m, int W, int lgW, int level,
+                                                           int* parent) {
+  const Dev& d = m.d;
+  const unsigned long long* Fp = m.F[(level - 1) & 1];
+  const unsigned long long* Fn = m.F[level & 1];
+  const int lane = threadIdx.x & 31;
+  const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  const long long nunits = min((long long)d.ctl->units, d.units_cap);
+  for (long long ui = wid; ui < nunits; ui += nw) {
+    const int2 un = d.units[ui];
+    const long long u = un.x;
+    const int pu = __ldg(d.perm + u);
+    const int end = min(__ldg(d.rdeg + u), un.y + PUSH_UNIT);
+    const long long chunk = u / d.C;
+    const long long base = __ldg(d.cs + chunk) + (u - chunk * d.C);
+    for (int ww = 0; ww < W; ++ww) {
+      const unsigned long long fu = __ldg(Fp + (u << lgW) + ww);
+      if (!fu) continue;
+      for (int j = un.y + lane; j < end; j += 32) {
+        const int v = __ldg(d.col + base + (long long)j * d.C);
+        unsigned long long g = __ldcg(Fn + ((long long)v << lgW) + ww) & fu;
+        if (!g) continue;
+        int* prow = parent + (long long)__ldg(d.perm + v) * m.k + 64 * ww;
+        while (g) {
+          atomicMax(prow + (__ffsll((long long)g) - 1), pu);
+          g &= g - 1;
         }
       }
     }
@@ -467,6 +547,10 @@ extern "C" ss_status slimsell_bfs_multi_parents(slimsell_handle h, const int32_t
   int lgW = 0;
   while ((1 << lgW) < W) ++lgW;
   SS_CUDA(cudaGetLastError());
+  if (d_parent) {  // the first frontier's edges (the roots' rows), for the parents pass
+    SS_CUDA(cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    SS_CUDA(cudaStreamSynchronize(st));
+  }
   const IterLaunch il{policy, 0, 0};
   const long long max_iter = (long long)h->n + 2;
   for (long long it = 0;; ++it) {
@@ -478,7 +562,20 @@ extern "C" ss_status slimsell_bfs_multi_parents(slimsell_handle h, const int32_t
     s = launch_multi(h, m, W, policy == SS_V_SLIMWORK, il, st);
     if (s != SS_OK) return s;
     if (d_parent) {  // parents of the sources gained at this level
-      k_multi_parents<<<8 * h->num_sms, 256, 0, st>>>(m, W, lgW, (int)(it + 1), d_parent);
+      // push from the previous frontier while the run grows and that frontier's
+      // rows carry at most 1 / MULTI_PAR_PUSH_SHARE of the edges (the gaining
+      // rows would have to search deep into their rows for it); once the
+      // frontiers are dense or shrinking, the gaining rows find their parents
+      // within a few neighbours and walk (measured on Kronecker 22, k = 64 ..
+      // 1024: the push wins levels 1 and 2 by 7-70x, the walk every later level)
+      const Ctl& hc = *h->h_ctl;  // counters read after the previous level
+      const bool growing = hc.prev_new >= hc.prev2_new;
+      if (growing && hc.prev_rowdeg * MULTI_PAR_PUSH_SHARE <= (unsigned long long)h->nnz) {
+        SS_CUDA(cudaMemsetAsync(&h->ctl->units, 0, sizeof(unsigned long long), st));
+        k_multi_par_expand<<<8 * h->num_sms, 256, 0, st>>>(m, (int)(it + 1));
+        k_multi_par_scatter<<<8 * h->num_sms, 256, 0, st>>>(m, W, lgW, (int)(it + 1), d_parent);
+      } else
+        k_multi_parents<<<8 * h->num_sms, 256, 0, st>>>(m, W, lgW, (int)(it + 1), d_parent);
       SS_CUDA(cudaGetLastError());
     }
     if (prof) SS_CUDA(cudaEventRecord(h->ev_b, st));

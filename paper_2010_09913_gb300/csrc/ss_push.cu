@@ -27,31 +27,7 @@ namespace ss {
 
 namespace cg = cooperative_groups;
 
-constexpr int PUSH_UNIT = 256;
 constexpr int PUSH_THREADS = 256;
-
-// Emit the work units of frontier vertex u (deg > 0), warp-aggregated.  All
-// lanes of the warp call; lanes with u < 0 emit nothing.
-__device__ __forceinline__ void emit_units(const Dev& d, int u, int lane) {
-  const int deg = (u >= 0) ? d.rdeg[u] : 0;
-  const unsigned nu = (unsigned)((deg + PUSH_UNIT - 1) / PUSH_UNIT);
-  unsigned incl = nu;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned t = __shfl_up_sync(SS_FULL_MASK, incl, o);
-    if (lane >= o) incl += t;
-  }
-  const unsigned total = __shfl_sync(SS_FULL_MASK, incl, 31);
-  unsigned long long base = 0;
-  if (lane == 31 && total) base = atomicAdd(&d.ctl->units, (unsigned long long)total);
-  base = __shfl_sync(SS_FULL_MASK, base, 31);
-  const unsigned long long first = base + incl - nu;
-  if (first + nu > (unsigned long long)d.units_cap) {  // cannot happen after the decide check
-    if (nu) atomicOr(&d.ctl->error, 2);
-    return;
-  }
-  for (unsigned q = 0; q < nu; ++q) d.units[first + q] = make_int2(u, (int)(q * PUSH_UNIT));
-}
 
 __global__ void __launch_bounds__(PUSH_THREADS) k_push_expand(Dev d) {
   const Ctl* c = d.ctl;
