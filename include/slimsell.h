@@ -366,13 +366,20 @@ typedef enum {
   SS_OPT_SELECTOR_MARGIN = 4, /* learned policy, in thousandths of a log-time unit, 0 .. 100000
                              (default 0): the network's choice replaces the frontier-size rule's
                              only when it predicts a gain larger than this margin             */
-  SS_OPT_PROFILE_QUEUE = 5 /* host-driven loop (profiling on, or SS_OPT_DEVICE_LOOP = 0) with a
+  SS_OPT_PROFILE_QUEUE = 5, /* host-driven loop (profiling on, or SS_OPT_DEVICE_LOOP = 0) with a
                              fixed variant (FULL, SLIMWORK, PULL_FILTERED): 1 (default) queues
                              the iterations eight at a time, each launch between its own pair of
                              CUDA events, and reads the run's counter once per batch (launches
                              past the end of the run return at once); 0: one launch, one event
                              pair and one counter read per iteration, as for the adaptive
                              policies                                                         */
+  SS_OPT_PUSH_BLOCKS = 6   /* the push variant's view of the frontier f_{k-1} (block-sparse with
+                             the layout's block size C, after the paper's closing author note):
+                             1 (default) chunks whose block holds at least C/4 frontier rows are
+                             pushed as blocks, reading whole columns of the chunk with coalesced
+                             16-byte loads, the other frontier rows one row each (stride C);
+                             2: every non-empty block as a block; 0: every frontier row alone.
+                             Results do not depend on it                                      */
 } ss_option;
 
 /* Set a handle option (applies to later calls).  Errors: SS_ERR_INVALID. */

@@ -1061,6 +1061,14 @@ ss_status slimsell_set_option(slimsell_handle h, int32_t option, int64_t value) 
     case SS_OPT_PROFILE_QUEUE:
       h->profile_queue = value ? 1 : 0;
       return SS_OK;
+    case SS_OPT_PUSH_BLOCKS:
+      if (value < 0 || value > 2) {
+        ss::set_error("slimsell_set_option: push blocks must be 0, 1 or 2");
+        return SS_ERR_INVALID;
+      }
+      h->push_blocks = (int)value;
+      ss::drop_loop_graphs(h);  // captured loops hold the previous value
+      return SS_OK;
     case SS_OPT_SELECTOR_MARGIN:
       if (value < 0 || value > 100000) {
         ss::set_error("slimsell_set_option: selector margin must be in [0, 100000] thousandths");

@@ -543,6 +543,9 @@ static ss_status alloc_state(slimsell_graph* h) {
   if ((s = dmalloc(h, (void**)&h->arrive, sizeof(unsigned) * ns)) != SS_OK) return s;
   h->units_cap = (long long)np + h->nnz / 256 + 1024;  // any frontier fits
   if ((s = dmalloc(h, (void**)&h->units, sizeof(int2) * (size_t)h->units_cap)) != SS_OK) return s;
+  // block units cover PUSH_BLOCK_SLOTS / C columns each: at most one partial unit per chunk
+  h->bunits_cap = (long long)h->n_c + h->slots / PUSH_BLOCK_SLOTS + 1024;
+  if ((s = dmalloc(h, (void**)&h->bunits, sizeof(int2) * (size_t)h->bunits_cap)) != SS_OK) return s;
   if ((s = dmalloc(h, (void**)&h->pbest, sizeof(int) * np)) != SS_OK) return s;
   if ((s = dmalloc(h, (void**)&h->psum, sizeof(float) * np)) != SS_OK) return s;
   if ((s = dmalloc(h, (void**)&h->touched, sizeof(unsigned) * (size_t)h->fb_words)) != SS_OK) return s;
@@ -592,7 +595,7 @@ void free_handle(slimsell_graph* h) {
   bc_release(h);
   void* ptrs[] = {h->perm, h->invperm, h->rdeg, h->cl, h->cs, h->col, h->items, h->split_n,
                   h->lvl, h->act, h->fb[0], h->fb[1], h->fr, h->par, h->xacc, h->xpar,
-                  h->arrive, h->ctl, h->iters, h->units, h->pbest,
+                  h->arrive, h->ctl, h->iters, h->units, h->bunits, h->pbest,
                   h->psum, h->touched, h->qlist[0], h->qlist[1], h->qdeg[0], h->qdeg[1], h->qbase[0],
                   h->qbase[1], h->qorig[0], h->qorig[1], h->qovf, h->qovf_n, h->lstat, h->mlp, h->feats, h->mF[0],
                   h->mF[1], h->mV, h->mxacc, h->mroots};
@@ -628,6 +631,7 @@ ss::Dev slimsell_graph::dev() const {
   d.smem_words = (int)(need < cap ? need : cap);
   d.fr = fr; d.par = par; d.xacc = xacc; d.xpar = xpar; d.arrive = arrive;
   d.units = units; d.units_cap = units_cap;
+  d.bunits = bunits; d.bunits_cap = bunits_cap; d.push_blocks = push_blocks;
   d.pbest = pbest; d.psum = psum; d.touched = touched; d.mlp = mlp; d.feats = feats;
   d.sel_margin = sel_margin;
   for (int b = 0; b < 2; ++b) {

@@ -70,6 +70,7 @@ struct Ctl {
   unsigned long long qlen[2];     // vertex-list lengths, by level parity
   unsigned long long qprep;       // length of a list just built from the bitmap
   unsigned long long loop_guard;  // decide-kernel executions in this run (device loop bound)
+  unsigned long long bunits;      // push block units queued by the current iteration
   unsigned long long new_rowdeg;  // multi-source: degree sum of the rows that gained a source
                                   // in the current iteration (each row counted once)
   unsigned long long prev_rowdeg; // ... in the previous iteration
@@ -98,6 +99,10 @@ struct Dev {
   unsigned* arrive;     // [n_split] SlimChunk arrival counters
   int2* units;          // [units_cap] push work units (row, first neighbour index)
   long long units_cap;
+  int2* bunits;         // [bunits_cap] push block units (chunk, first column) of the
+                        // block-sparse frontier: chunks whose frontier block is dense
+  long long bunits_cap;
+  int push_blocks;      // 0: vertex units only, 1: block units for dense blocks, 2: for every block
   int* pbest;           // [n_pad] push: largest frontier-neighbour original id (-1 = none yet,
                         // SS_PBEST_VISITED once the vertex has a level)
   float* psum;          // [n_pad] push: real-semiring sum of frontier-neighbour values
@@ -161,6 +166,9 @@ struct slimsell_graph {
   unsigned* arrive = nullptr;
   int2* units = nullptr;
   long long units_cap = 0;
+  int2* bunits = nullptr;
+  long long bunits_cap = 0;
+  int push_blocks = 1;                 // see SS_OPT_PUSH_BLOCKS
   int* pbest = nullptr;
   float* psum = nullptr;
   unsigned* touched = nullptr;

@@ -19,6 +19,8 @@ __device__ __forceinline__ bool local_fits(const Dev& d, unsigned long long nf, 
 // Neighbours per push work unit: a frontier row of degree D becomes ceil(D / PUSH_UNIT)
 // units (row, first neighbour index), so hub rows spread over many warps.
 constexpr int PUSH_UNIT = 256;
+// Slots per push block unit (PUSH_BLOCK_SLOTS / C columns of one chunk).
+constexpr int PUSH_BLOCK_SLOTS = 2048;
 
 // Emit the work units of frontier vertex u (deg > 0), warp-aggregated.  All
 // lanes of the warp call; lanes with u < 0 emit nothing.
@@ -81,6 +83,7 @@ __device__ __forceinline__ bool advance_level(const Dev& d, Ctl* c, int k, unsig
   c->variant = variant;
   if (variant >= 0 && variant < N_VARIANTS) c->variant_count[variant] += 1;
   c->units = 0;
+  c->bunits = 0;
   c->qprep = 0;
   bool stop = (nc == 0);
   if (k >= d.n + 1 || c->reached > d.reach_cap) {
@@ -229,6 +232,7 @@ __device__ __forceinline__ void init_root_state(const Dev& d, int root) {
   c->prev_variant = -1; c->prev_slots = 0; c->prev_new = 1; c->prev_deg = (unsigned long long)d.rdeg[r];
   c->prev2_new = 0; c->prev_active = 0; c->new_maxdeg = 0; c->prev_maxdeg = (unsigned)d.rdeg[r];
   c->units = 0;
+  c->bunits = 0;
   for (int v = 0; v < N_VARIANTS; ++v) c->variant_count[v] = 0;
   c->loop_guard = 0;
   c->list_level = -1; c->list_prev_ok = 0; c->qlen[0] = c->qlen[1] = 0; c->qprep = 0;

@@ -250,7 +250,7 @@ __global__ void k_multi_roots(MultiDev m, int W, int* parent) {
     c->reached = (unsigned long long)m.k; c->reached_deg = rd;
     c->total_slots = 0; c->dp_slots = 0; c->blocks_done = 0;
     c->prev_variant = -1; c->prev_slots = 0; c->prev_new = (unsigned long long)m.k; c->prev_deg = rd;
-    c->prev2_new = 0; c->prev_active = 0; c->new_maxdeg = 0; c->prev_maxdeg = 0; c->units = 0;
+    c->prev2_new = 0; c->prev_active = 0; c->new_maxdeg = 0; c->prev_maxdeg = 0; c->units = 0; c->bunits = 0;
     c->loop_guard = 0;
     for (int v = 0; v < N_VARIANTS; ++v) c->variant_count[v] = 0;
     c->list_level = -1; c->list_prev_ok = 0; c->qlen[0] = c->qlen[1] = 0; c->qprep = 0;

@@ -29,6 +29,48 @@ namespace cg = cooperative_groups;
 
 constexpr int PUSH_THREADS = 256;
 
+// The frontier bits of one chunk (bit l = row l of the chunk) in a 64-bit word.
+template <int C>
+__device__ __forceinline__ unsigned long long chunk_bits(const unsigned* fb, long long chunk) {
+  if (C == 8) return reinterpret_cast<const unsigned char*>(fb)[chunk];
+  if (C == 16) return reinterpret_cast<const unsigned short*>(fb)[chunk];
+  if (C == 32) return fb[chunk];
+  const uint2 v = reinterpret_cast<const uint2*>(fb)[chunk];
+  return ((unsigned long long)v.y << 32) | v.x;
+}
+
+// Emit the block units (chunk, first column) of chunk i, warp-aggregated; all
+// lanes call, lanes with i < 0 emit nothing.
+template <int C>
+__device__ __forceinline__ void emit_block_units(const Dev& d, long long i, int lane) {
+  constexpr int COLS = PUSH_BLOCK_SLOTS / C;
+  const int cl = (i >= 0) ? d.cl[i] : 0;
+  const unsigned nu = (unsigned)((cl + COLS - 1) / COLS);
+  unsigned incl = nu;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned t = __shfl_up_sync(SS_FULL_MASK, incl, o);
+    if (lane >= o) incl += t;
+  }
+  const unsigned total = __shfl_sync(SS_FULL_MASK, incl, 31);
+  unsigned long long base = 0;
+  if (lane == 31 && total) base = atomicAdd(&d.ctl->bunits, (unsigned long long)total);
+  base = __shfl_sync(SS_FULL_MASK, base, 31);
+  const unsigned long long first = base + incl - nu;
+  if (first + nu > (unsigned long long)d.bunits_cap) {  // cannot happen: the capacity covers every chunk
+    if (nu) atomicOr(&d.ctl->error, 2);
+    return;
+  }
+  for (unsigned q = 0; q < nu; ++q) d.bunits[first + q] = make_int2((int)i, (int)(q * COLS));
+}
+
+// The frontier f_{k-1} as work: walked one chunk (one block of C rows, the
+// layout's own block size) per lane.  With push_blocks on, a chunk whose block
+// holds at least C/4 frontier rows (all non-empty blocks with push_blocks = 2)
+// becomes block units that read whole columns of the chunk with coalesced
+// loads, the block-sparse frontier; the rows of sparser blocks become vertex
+// units that read one row each (stride C).  Also clears the touched map.
+template <int C>
 __global__ void __launch_bounds__(PUSH_THREADS) k_push_expand(Dev d) {
   const Ctl* c = d.ctl;
   if (c->done) return;
@@ -38,20 +80,38 @@ __global__ void __launch_bounds__(PUSH_THREADS) k_push_expand(Dev d) {
   const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long words = ((long long)d.n_pad + 31) / 32;
   for (long long w = t0; w < words; w += stride) d.touched[w] = 0u;
-  const long long wstride = stride & ~31LL;  // whole warps walk the bitmap together
+  const long long wstride = stride & ~31LL;  // whole warps walk the chunks together
   const unsigned* fbm = d.fb[(k - 1) & 1];
-  for (long long i0 = t0 - lane; i0 < words; i0 += wstride) {
+  for (long long i0 = t0 - lane; i0 < d.n_c; i0 += wstride) {
     const long long i = i0 + lane;
-    unsigned bits = i < words ? fbm[i] : 0u;
-    while (__any_sync(SS_FULL_MASK, bits != 0u)) {
+    unsigned long long bits = i < d.n_c ? chunk_bits<C>(fbm, i) : 0ull;
+    const int pc = __popcll(bits);
+    const bool block = bits && (d.push_blocks == 2 || (d.push_blocks == 1 && pc >= C / 4));
+    if (__any_sync(SS_FULL_MASK, block)) emit_block_units<C>(d, block ? i : -1, lane);
+    if (block) bits = 0ull;
+    while (__any_sync(SS_FULL_MASK, bits != 0ull)) {
       int u = -1;
       if (bits) {
-        const int b = __ffs(bits) - 1;
+        const int b = __ffsll((long long)bits) - 1;
         bits &= bits - 1;
-        u = (int)(i * 32 + b);
+        u = (int)(i * C + b);
       }
       emit_units(d, u, lane);
     }
+  }
+}
+
+// Fold the frontier row (original id origu, real value val) into neighbour v
+// when v is unvisited.
+template <int SR>
+__device__ __forceinline__ void push_fold(const Dev& d, int v, int origu, float val) {
+  if (d.lvl[v] == SS_INF) {
+    // parents and touched bits only grow, so a stale read can only cause a
+    // redundant atomic, never a missed one
+    if (*(volatile const int*)(d.pbest + v) < origu) atomicMax(d.pbest + v, origu);
+    if (SR == SS_REAL) atomicAdd(d.psum + v, val);
+    const unsigned bit = 1u << (v & 31);
+    if (!(*(volatile const unsigned*)(d.touched + (v >> 5)) & bit)) atomicOr(d.touched + (v >> 5), bit);
   }
 }
 
@@ -76,14 +136,40 @@ __global__ void __launch_bounds__(PUSH_THREADS) k_push_scatter(Dev d) {
     for (int j = un.y + lane; j < jend; j += 32) {
       const int v = __ldg(rowp + (long long)j * C);
       ++my_slots;
-      if (d.lvl[v] == SS_INF) {
-        // parents and touched bits only grow, so a stale read can only cause a
-        // redundant atomic, never a missed one
-        if (*(volatile const int*)(d.pbest + v) < origu) atomicMax(d.pbest + v, origu);
-        if (SR == SS_REAL) atomicAdd(d.psum + v, val);
-        const unsigned bit = 1u << (v & 31);
-        if (!(*(volatile const unsigned*)(d.touched + (v >> 5)) & bit))
-          atomicOr(d.touched + (v >> 5), bit);
+      push_fold<SR>(d, v, origu, val);
+    }
+  }
+  // block units: columns [j0, j0 + COLS) of a chunk whose frontier block is
+  // dense, read as 16-byte quads (lane l meets rows 4 (l mod C/4) .. + 3 in
+  // every column); only the block's frontier rows fold their neighbours in
+  {
+    constexpr int Q = C / 4;
+    constexpr int COLS = PUSH_BLOCK_SLOTS / C;
+    const long long nb = min((long long)c->bunits, d.bunits_cap);
+    const unsigned* fbm = d.fb[(c->k - 1) & 1];
+    const int lq = lane % Q;
+    for (long long bi = wid; bi < nb; bi += nw) {
+      const int2 un = d.bunits[bi];
+      const long long chunk = un.x;
+      const unsigned mb = (unsigned)(chunk_bits<C>(fbm, chunk) >> (4 * lq)) & 0xFu;
+      const int ncols = min(COLS, d.cl[chunk] - un.y);
+      if (lane == 0) my_slots += (unsigned long long)ncols * C;
+      if (!mb) continue;  // none of this lane's rows is in the frontier
+      const long long r0 = chunk * C + 4 * lq;
+      int origs[4];
+      float vals[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        origs[r] = (mb >> r & 1u) ? __ldg(d.perm + r0 + r) : -1;
+        vals[r] = (SR == SS_REAL && (mb >> r & 1u)) ? d.fr[r0 + r] : 0.0f;
+      }
+      const int4* base = reinterpret_cast<const int4*>(d.col + d.cs[chunk] + (long long)un.y * C) + lq;
+      for (int j = lane / Q; j < ncols; j += 32 / Q) {
+        const int4 q = __ldcs(base + (long long)j * Q);
+        const int cc[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          if ((mb >> r & 1u) && cc[r] >= 0) push_fold<SR>(d, cc[r], origs[r], vals[r]);
       }
     }
   }
@@ -797,7 +883,7 @@ static ss_status launch_push_c(const slimsell_graph* h, const Dev& d, const Iter
   const int gw = vertex_grid(h, 32 * PUSH_THREADS);
   const long long units = (long long)h->n_pad + h->nnz / PUSH_UNIT;
   const int gs = (int)std::max(1LL, std::min((long long)8 * h->num_sms, (units + 7) / 8));
-  k_push_expand<<<gw, PUSH_THREADS, 0, st>>>(d);
+  k_push_expand<C><<<gw, PUSH_THREADS, 0, st>>>(d);
   k_push_scatter<SR, C><<<gs, PUSH_THREADS, 0, st>>>(d);
   k_push_post<SR><<<gw, PUSH_THREADS, 0, st>>>(d, il);
   SS_CUDA(cudaGetLastError());

@@ -267,3 +267,31 @@ def _kron22_handle():
         g = _kron22()
         _cache["G"] = ss.SlimSellGraph.from_host(g.row_ptr, g.col, C=32, sigma=g.n, split_w=1024)
     return _cache["G"]
+
+
+@pytest.mark.parametrize("blocks", [0, 1, 2])
+def test_push_block_sparse_frontier(blocks):
+    """The push variant with the frontier seen block-sparse (chunks of C rows
+    pushed as blocks with coalesced column reads), per row, or mixed: every
+    semiring, C, sigma (sigma = 1 pads hub chunks heavily) and split width give
+    the oracle's distances and parents, for the push policy and the adaptive
+    schedules that use it."""
+    graphs = [gg.kronecker(13, seed=9), gg.lattice(40, 0.05, seed=4), gg.erdos_renyi(3000, 6.0, seed=5)]
+    for g in graphs:
+        for C, sigma, split_w in [(32, 0, 256), (8, 1, 16), (64, 128, 0), (16, 1, 64)]:
+            G = ss.SlimSellGraph.from_host(g.row_ptr, g.col, C=C, sigma=sigma or g.n, split_w=split_w)
+            G.set_option(ss.OPT_PUSH_BLOCKS, blocks)
+            for r in gg.roots(g, 2, seed=13):
+                d, p = expected(g, r)
+                for sr in SEMIRINGS:
+                    for pol in ("push", "heuristic"):
+                        dist, parent = run(G, r, sr, pol)
+                        np.testing.assert_array_equal(dist, d, err_msg=f"{g.name} C={C} {sr} {pol}")
+                        np.testing.assert_array_equal(parent, p, err_msg=f"{g.name} C={C} {sr} {pol}")
+            G.close()
+    with pytest.raises(ss.SlimSellError):
+        G = ss.SlimSellGraph.from_host(graphs[0].row_ptr, graphs[0].col)
+        try:
+            G.set_option(ss.OPT_PUSH_BLOCKS, 3)
+        finally:
+            G.close()
