@@ -576,10 +576,11 @@ def format_ab(ss, torch, g, sigmas, stream, dev, nroots=4):
     return out
 
 
-def bc_measure(ss, torch, g, h, stream, dev, nsources=8):
-    """Betweenness centrality (Brandes, fp64) over `nsources` seeded sources on
-    the benchmark graph's handle: summed device time of the level kernels and
-    TEPS = sources * undirected edges / time."""
+def bc_measure(ss, torch, g, h, stream, dev, nsources=64):
+    """Betweenness centrality (Brandes, fp64) over `nsources` seeded sources (one
+    batch of the bit-packed multi-source passes) on the benchmark graph's
+    handle: summed device time of the level kernels and TEPS = sources *
+    undirected edges / time."""
     src = torch.from_numpy(gg.roots(g, nsources, seed=11)).to(dev)
     out = torch.empty(g.n, dtype=torch.float64, device=dev)
     ss.slimsell_bc(h, src[:1], out, stream)  # warm-up (allocates the scratch)

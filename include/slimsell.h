@@ -238,17 +238,21 @@ ss_status slimsell_bfs_spmv(slimsell_handle h, int32_t root, int32_t semiring, i
  * (sigma_st = number of shortest s-t paths, sigma_st(v) those through v).  On
  * an undirected graph with every vertex as a source each unordered pair counts
  * twice; halve for the one-direction convention.
- * Per source: a forward pull per level over the rows not yet reached sums the
- * path counts of neighbours one level up (the real-semiring BFS step with the
- * counts kept), then a backward pull per level from the deepest level sums
- * (1 + delta(w)) / sigma(w) over neighbours one level down.  fp64 throughout;
- * split chunks (SlimChunk) combine with atomicAdd, so the result may differ
- * from a serial sum in the last bits.
+ * Sources go in batches of 64.  Per batch, the bit-packed multi-source BFS
+ * (slimsell_bfs_multi's SlimWork pull) finds the level words of every vertex
+ * (bit s set at level L when the vertex is at distance L from source s); a
+ * forward pass per level sums the path counts sigma of the neighbours one
+ * level up, per source (the real-semiring BFS step with the counts kept), and a
+ * backward pass per level from the deepest sums (1 + delta(w)) / sigma(w) over
+ * the neighbours one level down.  fp64 throughout; a row's neighbours are cut
+ * into units of 256 that combine with atomicAdd, so the result may differ from
+ * a serial sum in the last bits.
  *   d_sources int32[k] device, k >= 1, each in [0, n) (copied to the host)
  *   d_bc      double[n] device, overwritten
  *   kernel_ms host double* or NULL: summed device time of the level kernels
- * Synchronous with respect to the host.  Scratch (28 bytes per row) is
- * allocated on first use and kept until slimsell_destroy.
+ * Synchronous with respect to the host.  Scratch (1.5 KB per row, plus 8 bytes
+ * per row and level) is allocated on first use and kept until
+ * slimsell_destroy; the call also uses the multi-source scratch.
  * Errors: SS_ERR_INVALID (NULL, k < 1, a source out of range), SS_ERR_OOM,
  *         SS_ERR_CUDA.
  */

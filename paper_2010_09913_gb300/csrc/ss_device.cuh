@@ -253,6 +253,24 @@ __device__ __forceinline__ void write_outputs(const Dev& d, int* dist, int* pare
   }
 }
 
+// View of a multi-source BFS run (ss_multi.cu): F[level & 1][row * W + w] holds bit s of
+// word w when row entered source 64 w + s's frontier at that level; V the visited bits.
+struct MultiDev {
+  Dev d;
+  unsigned long long* F[2];
+  unsigned long long* V;
+  unsigned long long* xacc;  // [n_split][C][W]
+  int* dist;                 // [n][k] in original vertex order, or NULL
+  int vec_dist;              // k % 4 == 0 and dist 16-byte aligned: 16-byte group writes
+  const int* roots;          // [k]
+  int k;
+};
+
+ss_status multi_start(slimsell_graph* h, const int32_t* d_roots, int k, cudaStream_t st, MultiDev* m,
+                      int* W_out);
+ss_status multi_level(slimsell_graph* h, const MultiDev& m, int W, cudaStream_t st, bool* done,
+                      cudaEvent_t before = nullptr, cudaEvent_t after = nullptr);
+
 __global__ void k_init(Dev d);
 
 // Grid sizes that follow the graph size (ss_bfs.cu).

@@ -41,17 +41,6 @@ constexpr int MULTI_BATCH = SS_MULTI_BATCH;  // columns per thread in flight
 #define SS_MULTI_BLOCKS_PER_SM 0  // resident blocks per SM (0: as many as fit)
 #endif
 
-struct MultiDev {
-  Dev d;
-  unsigned long long* F[2];
-  unsigned long long* V;
-  unsigned long long* xacc;  // [n_split][C][W]
-  int* dist;                 // [n][k] in original vertex order, or NULL
-  int vec_dist;              // k % 4 == 0 and dist 16-byte aligned: 16-byte group writes
-  const int* roots;          // [k]
-  int k;
-};
-
 // Distances of the new sources (bits of nb) of one 64-source word, in 16-byte
 // groups of 4: a group with no earlier discovery (bits of vold) still holds -1
 // everywhere and is written whole; otherwise it is read first.  Kept out of line
@@ -481,6 +470,55 @@ static ss_status ensure_multi_scratch(slimsell_graph* h, int W) {
   if ((s = dmalloc(h, (void**)&h->mxacc, sizeof(unsigned long long) * ns)) != SS_OK) return s;
   if ((s = dmalloc(h, (void**)&h->mroots, sizeof(int) * 1024)) != SS_OK) return s;
   h->multi_w = W;
+  return SS_OK;
+}
+
+// Level-by-level multi-source BFS for the passes built on it (betweenness
+// centrality): seeds k sources (device ids, checked by the caller) and returns
+// the view of the handle's multi-source state; multi_level then runs one level
+// (SlimWork pull) and reports whether it discovered nothing.  The frontier words
+// of level L are m->F[L & 1] (W words per row) until level L + 2 overwrites them.
+// Optional events are recorded around the level's kernel.
+ss_status multi_start(slimsell_graph* h, const int32_t* d_roots, int k, cudaStream_t st, MultiDev* m,
+                      int* W_out) {
+  int W = 1;
+  while (64 * W < k) W *= 2;
+  while (h->C * W < 32) W *= 2;
+  if (h->pending) SS_CUDA(cudaEventSynchronize(h->ev_done));
+  h->pending = 0;
+  ss_status s = ensure_multi_scratch(h, W);
+  if (s != SS_OK) return s;
+  SS_CUDA(cudaMemcpyAsync(h->mroots, d_roots, sizeof(int) * (size_t)k, cudaMemcpyDeviceToDevice, st));
+  m->d = h->dev();
+  m->d.reach_cap = (unsigned long long)h->n * (unsigned long long)k;
+  m->F[0] = h->mF[0];
+  m->F[1] = h->mF[1];
+  m->V = h->mV;
+  m->xacc = h->mxacc;
+  m->dist = nullptr;
+  m->vec_dist = 0;
+  m->roots = h->mroots;
+  m->k = k;
+  k_multi_init<<<8 * h->num_sms, 256, 0, st>>>(*m, W);
+  k_multi_roots<<<(k + 255) / 256, 256, 0, st>>>(*m, W, nullptr);
+  SS_CUDA(cudaGetLastError());
+  *W_out = W;
+  return SS_OK;
+}
+
+ss_status multi_level(slimsell_graph* h, const MultiDev& m, int W, cudaStream_t st, bool* done,
+                      cudaEvent_t before, cudaEvent_t after) {
+  if (before) SS_CUDA(cudaEventRecord(before, st));
+  ss_status s = launch_multi(h, m, W, true, IterLaunch{SS_V_SLIMWORK, 0, 0}, st);
+  if (s != SS_OK) return s;
+  if (after) SS_CUDA(cudaEventRecord(after, st));
+  SS_CUDA(cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaStreamSynchronize(st));
+  if (h->h_ctl->error) {
+    set_error("multi-source BFS: device error flags %d", h->h_ctl->error);
+    return SS_ERR_CUDA;
+  }
+  *done = h->h_ctl->done != 0;
   return SS_OK;
 }
 
