@@ -177,11 +177,13 @@ __device__ __forceinline__ void finish_iteration_block(const Dev& d, unsigned lo
 // fp32 throughout: double-precision transcendentals are very slow on this GPU.
 __device__ __forceinline__ float feat_lg(float x) { return __log2f(1.0f + fmaxf(x, 0.0f)); }
 
+// Every feature describes the BFS state, never the schedule that reached it
+// (a feature of the previous pass's work, for instance, reads 0 after levels
+// the cluster push ran and would mislead the network there).
 __device__ __forceinline__ void features_of(const Dev& d, int k, unsigned long long prev_new,
                                             unsigned long long prev_deg, unsigned long long reached,
-                                            unsigned long long reached_deg, unsigned long long prev_active,
-                                            unsigned long long prev_slots, unsigned prev_maxdeg,
-                                            unsigned long long prev2_new, bool first, float* f) {
+                                            unsigned long long reached_deg, unsigned prev_maxdeg,
+                                            unsigned long long prev2_new, float* f) {
   const float n = (float)d.n, nnz = (float)(d.nnz > 0 ? d.nnz : 1);
   const float nf = (float)prev_new, mf = (float)prev_deg;
   const float unv = (float)((unsigned long long)d.n - reached);
@@ -192,8 +194,8 @@ __device__ __forceinline__ void features_of(const Dev& d, int k, unsigned long l
   f[3] = mf / nnz;
   f[4] = feat_lg(unv) / 32.f;
   f[5] = unv / n;
-  f[6] = first ? 1.f : (float)prev_active / (float)(d.n_c > 0 ? d.n_c : 1);
-  f[7] = first ? 1.f : (float)prev_slots / (float)(d.total_slots > 0 ? d.total_slots : 1);
+  f[6] = mu / nnz;                      // share of the edge endpoints still unexplored
+  f[7] = mf / fmaxf(mf + mu, 1.f);      // frontier edges against the unexplored ones
   f[8] = (float)k / 32.f;
   f[9] = (float)k / (float)(k + 1);
   f[10] = feat_lg(mf / fmaxf(nf, 1.f)) / 32.f;
@@ -205,8 +207,7 @@ __device__ __forceinline__ void features_of(const Dev& d, int k, unsigned long l
 }
 
 __device__ __forceinline__ void compute_features(const Dev& d, const Ctl* c, float* f) {
-  features_of(d, c->k, c->prev_new, c->prev_deg, c->reached, c->reached_deg, c->prev_active, c->prev_slots,
-              c->prev_maxdeg, c->prev2_new, c->prev_variant < 0, f);
+  features_of(d, c->k, c->prev_new, c->prev_deg, c->reached, c->reached_deg, c->prev_maxdeg, c->prev2_new, f);
 }
 
 // Write the features of iteration k into d.feats (one thread).

@@ -83,8 +83,10 @@ __global__ void __launch_bounds__(C * W) k_multi_pull(MultiDev m, IterLaunch il)
   unsigned* FAn = d.fb[level & 1];
   __shared__ int s_flag;
   __shared__ unsigned s_fa[2];
-  unsigned long long nw = 0, deg = 0, slots = 0, act = 0, rowdeg = 0;
+  unsigned long long nw = 0, deg = 0, slots = 0, act = 0;
   unsigned maxdeg = 0;
+  __shared__ unsigned long long s_rowdeg;  // degree sum of the block's rows that gained a source
+  if (tid == 0) s_rowdeg = 0ull;
   for (int it = blockIdx.x; it < d.n_items; it += gridDim.x) {
     const int4 item = d.items[it];
     const int chunk = item.x;
@@ -171,7 +173,7 @@ __global__ void __launch_bounds__(C * W) k_multi_pull(MultiDev m, IterLaunch il)
     }
     Fn[row * W + w] = nb;
     const int left = __syncthreads_or((vold | nb) != ~0ull);
-    if (w == 0 && ((s_fa[r >> 5] >> (r & 31)) & 1u)) rowdeg += (unsigned long long)d.rdeg[row];
+    if (w == 0 && ((s_fa[r >> 5] >> (r & 31)) & 1u)) atomicAdd(&s_rowdeg, (unsigned long long)d.rdeg[row]);
     if (tid == 0) {
       store_summary<C>(FAn, chunk, s_fa[0], s_fa[1]);
       d.act[chunk] = left ? 1 : 3;
@@ -180,10 +182,9 @@ __global__ void __launch_bounds__(C * W) k_multi_pull(MultiDev m, IterLaunch il)
   }
   // degree sum of the rows that gained a source, each row counted once (the
   // parents pass picks its direction from it)
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) rowdeg += __shfl_down_sync(SS_FULL_MASK, rowdeg, off);
-  if ((tid & 31) == 0 && rowdeg) {
-    atomicAdd(&c->new_rowdeg, rowdeg);
+  __syncthreads();
+  if (tid == 0 && s_rowdeg) {
+    atomicAdd(&c->new_rowdeg, s_rowdeg);
     __threadfence();  // before this block counts itself done
   }
   finish_iteration_block<T>(d, nw, deg, slots, act, maxdeg, il);

@@ -393,7 +393,7 @@ __device__ __forceinline__ void local_features(const Dev& d, LocalSmem& S, cg::c
   for (int k = k0 + (int)threadIdx.x; k <= k1 && k + 1 < d.iter_cap; k += LOCAL_THREADS) {
     const unsigned long long* ls = d.lstat + (size_t)k * SS_LSTAT;
     float f[SS_SELECTOR_FEATURES];
-    features_of(d, k + 1, ls[0], ls[1], ls[4], ls[5], 0ull, ls[3], (unsigned)ls[2], ls[6], false, f);
+    features_of(d, k + 1, ls[0], ls[1], ls[4], ls[5], (unsigned)ls[2], ls[6], f);
     store_features(d, k + 1, f);
   }
 }

@@ -26,6 +26,8 @@ constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + F_IN * F_H, OFF_W2 = OFF_B1 + F_H,
 static_assert(N_PARAMS == SS_SELECTOR_PARAMS, "selector parameter count");
 
 constexpr int PUSH_UNIT_SEL = 256;  // must match the push kernels' unit size
+constexpr int DECIDE_THREADS = 256;  // the decide block (the MLP uses its first F_H threads)
+static_assert(N_PARAMS % 4 == 0, "weights are staged as float4");
 
 // Frontier-size rule (top-down / bottom-up switching with alpha = 14, beta = 24).
 __device__ int heuristic_variant(const Dev& d, const Ctl* c) {
@@ -44,16 +46,21 @@ __device__ __forceinline__ bool push_fits(const Dev& d, const Ctl* c) {
   return need <= (unsigned long long)d.units_cap;
 }
 
-// One block of F_H threads.  Writes ctl->variant and sets the switch.  In the
+// One block of DECIDE_THREADS threads.  Writes ctl->variant and sets the switch.  In the
 // device-side loop it also ends the loop (WHILE condition 0) if the run is
 // already done or has looped more than n + 2 times, so termination never
 // depends on a later kernel.
-__global__ void k_decide(Dev d, int policy, cudaGraphConditionalHandle sw, int use_sw,
-                         cudaGraphConditionalHandle cw, int use_cw) {
+__global__ void __launch_bounds__(DECIDE_THREADS) k_decide(Dev d, int policy, cudaGraphConditionalHandle sw,
+                                                            int use_sw, cudaGraphConditionalHandle cw,
+                                                            int use_cw) {
   __shared__ float x[F_IN], h1[F_H], h2[F_H], y[F_OUT];
+  __shared__ __align__(16) float wsh[N_PARAMS];  // the selector weights, staged once per decision
   __shared__ int choice, stop;
   Ctl* c = d.ctl;
   const int t = threadIdx.x;
+  if (policy == SS_V_LEARNED && d.mlp != nullptr)  // in flight while thread 0 computes the features
+    for (int i = t; i < N_PARAMS / 4; i += DECIDE_THREADS)
+      reinterpret_cast<float4*>(wsh)[i] = __ldg(reinterpret_cast<const float4*>(d.mlp) + i);
   if (t == 0) {
     stop = c->done;  // host-driven queued loops launch past the end of a run
     if (use_cw) {
@@ -88,14 +95,19 @@ __global__ void k_decide(Dev d, int policy, cudaGraphConditionalHandle sw, int u
   }
   __syncthreads();
   if (policy == SS_V_LEARNED && d.mlp != nullptr) {
-    const float* W = d.mlp;
-    float a = W[OFF_B1 + t];
-    for (int i = 0; i < F_IN; ++i) a += x[i] * W[OFF_W1 + i * F_H + t];
-    h1[t] = fmaxf(a, 0.f);
+    const float* W = wsh;
+    float a = 0.f;
+    if (t < F_H) {
+      a = W[OFF_B1 + t];
+      for (int i = 0; i < F_IN; ++i) a += x[i] * W[OFF_W1 + i * F_H + t];
+      h1[t] = fmaxf(a, 0.f);
+    }
     __syncthreads();
-    a = W[OFF_B2 + t];
-    for (int i = 0; i < F_H; ++i) a += h1[i] * W[OFF_W2 + i * F_H + t];
-    h2[t] = fmaxf(a, 0.f);
+    if (t < F_H) {
+      a = W[OFF_B2 + t];
+      for (int i = 0; i < F_H; ++i) a += h1[i] * W[OFF_W2 + i * F_H + t];
+      h2[t] = fmaxf(a, 0.f);
+    }
     __syncthreads();
     if (t < F_OUT) {
       a = W[OFF_B3 + t];
@@ -134,7 +146,7 @@ __global__ void k_decide(Dev d, int policy, cudaGraphConditionalHandle sw, int u
 
 ss_status launch_decide(const slimsell_graph* h, const Dev& d, int policy,
                         cudaGraphConditionalHandle sw, int use_sw, cudaStream_t st) {
-  k_decide<<<1, F_H, 0, st>>>(d, policy, sw, use_sw, 0, 0);
+  k_decide<<<1, DECIDE_THREADS, 0, st>>>(d, policy, sw, use_sw, 0, 0);
   SS_CUDA(cudaGetLastError());
   return SS_OK;
 }
@@ -149,7 +161,7 @@ ss_status add_decide_node(const slimsell_graph* h, const Dev& d, int policy,
   cudaKernelNodeParams kp = {};
   kp.func = (void*)k_decide;
   kp.gridDim = dim3(1);
-  kp.blockDim = dim3(F_H);
+  kp.blockDim = dim3(DECIDE_THREADS);
   kp.sharedMemBytes = 0;
   kp.kernelParams = args;
   SS_CUDA(cudaGraphAddKernelNode(out, g, nullptr, 0, &kp));

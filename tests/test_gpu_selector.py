@@ -177,12 +177,14 @@ def test_selector_training_pipeline():
     # loop, median of 15 runs per root) on every training family: less time than
     # the plain SlimWork pass by a stated factor (5 % on the small Kronecker graph,
     # where the frontier-size rule itself gains about 15 %; half on the lattice,
-    # whose small levels go to the cluster push), and within 5 % of the rule (the
-    # rule is also its fallback, with the bench's margin of 0.1)
+    # whose small levels go to the cluster push), and within 5 % of the rule, its
+    # fallback: the network overrides the rule only where it predicts a gain of
+    # 0.3 log units (about 35 %), since labels of levels this small (10-30 us)
+    # carry launch overheads of the same size
     gain = [0.95, 0.5]
     for (G, g), factor in zip(handles, gain):
         ss.slimsell_selector_load(G.h, w)
-        G.set_option(ss.OPT_SELECTOR_MARGIN, 100)
+        G.set_option(ss.OPT_SELECTOR_MARGIN, 300)
         t = selector.device_times(G, gg.roots(g, 2, seed=4), "tropical",
                                   ["slimwork", "heuristic", "learned"])
         assert t["learned"] <= factor * t["slimwork"], (g.name, t)
