@@ -541,10 +541,12 @@ def roofline_at_scale(ss, torch, scale, nroots, split_w, stream, dev):
 
 
 def format_ab(ss, torch, g, sigmas, stream, dev, nroots=4):
-    """Speedup of SlimSell over Sell-C-sigma (Section IV): the plain value-vector
-    BFS-SpMV in both formats on the same layout (C = 32, SlimChunk w = 256), for
-    each sigma and semiring; summed device time of the iteration kernels over
-    `nroots` roots, each format warmed up once (which builds the Sell arrays)."""
+    """Speedup of SlimSell over Sell-C-sigma (Section IV) on the same layout (C =
+    32, SlimChunk w = 256), for each sigma and semiring: the plain value-vector
+    BFS-SpMV in both formats (summed device time of the iteration kernels), and
+    the production SlimWork pull streaming either format (device-side loops,
+    CUDA events around the runs); `nroots` roots, each format warmed up once
+    (which builds the Sell arrays)."""
     roots = gg.roots(g, nroots, seed=5)
     rp_d = torch.from_numpy(g.row_ptr).to(dev)
     col_d = torch.from_numpy(g.col).to(dev)
@@ -565,10 +567,28 @@ def format_ab(ss, torch, g, sigmas, stream, dev, nroots=4):
                 ss.slimsell_bfs_spmv(h, int(roots[0]), SR_ID[sr], f, dist, stream, timed=True)
                 ms[name] = sum(ss.slimsell_bfs_spmv(h, int(r), SR_ID[sr], f, dist, stream, timed=True)
                                for r in roots)
+            # the production pull (SlimWork, bitmaps, device-side loop) streaming
+            # either format: CUDA events around all roots' runs
+            pull = {}
+            for name, f in (("slimsell", ss.FORMAT_SLIMSELL), ("sell", ss.FORMAT_SELL)):
+                ss.slimsell_set_option(h, ss.OPT_FORMAT, f)
+                ss.slimsell_bfs(h, int(roots[0]), SR_ID[sr], ss.V_SLIMWORK, None, None, stream)  # warm
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                for r in roots:
+                    ss.slimsell_bfs(h, int(r), SR_ID[sr], ss.V_SLIMWORK, None, None, stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                pull[name] = e0.elapsed_time(e1)
+            ss.slimsell_set_option(h, ss.OPT_FORMAT, ss.FORMAT_SLIMSELL)
             row[sr] = {"slimsell_ms": ms["slimsell"], "sell_ms": ms["sell"],
                        "speedup_slimsell_over_sell": ms["sell"] / ms["slimsell"],
                        "gteps_slimsell": edges / (ms["slimsell"] / 1000.0) / 1e9,
-                       "gteps_sell": edges / (ms["sell"] / 1000.0) / 1e9}
+                       "gteps_sell": edges / (ms["sell"] / 1000.0) / 1e9,
+                       "pull_slimwork_slimsell_ms": pull["slimsell"], "pull_slimwork_sell_ms": pull["sell"],
+                       "pull_speedup_slimsell_over_sell": pull["sell"] / pull["slimsell"]}
         out[f"sigma_{inf.sigma}"] = row
         ss.slimsell_destroy(h)
         torch.cuda.empty_cache()

@@ -377,12 +377,20 @@ typedef enum {
                              past the end of the run return at once); 0: one launch, one event
                              pair and one counter read per iteration, as for the adaptive
                              policies                                                         */
-  SS_OPT_PUSH_BLOCKS = 6   /* the push variant's view of the frontier f_{k-1} (block-sparse with
+  SS_OPT_PUSH_BLOCKS = 6,  /* the push variant's view of the frontier f_{k-1} (block-sparse with
                              the layout's block size C, after the paper's closing author note):
                              1 (default) chunks whose block holds at least C/4 frontier rows are
                              pushed as blocks, reading whole columns of the chunk with coalesced
                              16-byte loads, the other frontier rows one row each (stride C);
                              2: every non-empty block as a block; 0: every frontier row alone.
+                             Results do not depend on it                                      */
+  SS_OPT_FORMAT = 8        /* storage format the pull streams (ss_format): SS_FORMAT_SLIMSELL
+                             (default), or SS_FORMAT_SELL: the same pull over the Sell-C-sigma
+                             arrays (column with padding 0 and an explicit value per slot: 1 for
+                             an edge, the semiring's zero for padding; built on first use, 12
+                             bytes per slot, kept until slimsell_destroy), for the format
+                             comparison of Section IV at the production kernel's speed; with the
+                             FULL and SLIMWORK policies only (others: SS_ERR_UNSUPPORTED).
                              Results do not depend on it                                      */
 } ss_option;
 

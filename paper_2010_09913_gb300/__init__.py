@@ -222,7 +222,7 @@ def slimsell_set_profiling(h: int, on: bool) -> None:
 
 
 OPT_DP_PASS, OPT_SMEM_BYTES, OPT_DEVICE_LOOP, OPT_SELECTOR_MARGIN, OPT_PROFILE_QUEUE = 1, 2, 3, 4, 5
-OPT_PUSH_BLOCKS = 6
+OPT_PUSH_BLOCKS, OPT_FORMAT = 6, 8
 
 
 def slimsell_set_option(h: int, option: int, value: int) -> None:

@@ -45,6 +45,9 @@ namespace ss {
 #ifndef SS_PULL_STEP_REAL
 #define SS_PULL_STEP_REAL 3  // the real semiring also gathers a value per hit
 #endif
+#ifndef SS_PULL_STEP_SELL
+#define SS_PULL_STEP_SELL 2  // Sell-C-sigma loads a value quad beside each column quad
+#endif
 #ifndef SS_PULL_PREFETCH
 #define SS_PULL_PREFETCH 0  // bulk L2 prefetch distance beyond the next step (0: next step only)
 #endif
@@ -59,8 +62,22 @@ constexpr int PULL_THREADS = SS_PULL_THREADS;  // one block per SM
 constexpr int SHORT_COLS = SS_PULL_SHORT_COLS;  // chunks this short go several per warp
 
 // int4 col loads in flight per lane (4 slots each)
+template <int SR, int FMT>
+__host__ __device__ constexpr int pull_step() {
+  return FMT == SS_FORMAT_SELL ? SS_PULL_STEP_SELL : (SR == SS_REAL ? SS_PULL_STEP_REAL : SS_PULL_STEP);
+}
+// Bits of the semiring's zero, the value of a Sell-C-sigma padding slot.
 template <int SR>
-__host__ __device__ constexpr int pull_step() { return SR == SS_REAL ? SS_PULL_STEP_REAL : SS_PULL_STEP; }
+__host__ __device__ constexpr int sell_zero_bits() { return SR == SS_TROPICAL ? 0x7f800000 : 0; }
+
+// A Sell-C-sigma quad read: the slots whose value is the semiring's zero are no
+// edges (padding, column 0) and become -1, so the scan treats them as SlimSell
+// padding; the values stay in v for the real semiring's multiply.
+template <int SR>
+__device__ __forceinline__ int4 sell_edges(int4 c, int4 v) {
+  constexpr int Z = sell_zero_bits<SR>();
+  return make_int4(v.x == Z ? -1 : c.x, v.y == Z ? -1 : c.y, v.z == Z ? -1 : c.z, v.w == Z ? -1 : c.w);
+}
 // Stage the bitmap prefix only when the previous iteration read at least this
 // many slots; below it, reading frontier bits from global memory is cheaper.
 constexpr unsigned long long STAGE_MIN_SLOTS = 2ull << 20;
@@ -245,11 +262,16 @@ __device__ __forceinline__ void carry_chunk(const Dev& d, int k, int chunk, int 
 // in shared memory (smf), the others from global memory.  (Skipping the bit
 // lookups of rows already hit, for the other semirings, measured slower: the
 // predicated lookups cost more issue slots than they save.)
-template <int SR>
+//
+// Sell-C-sigma (FMT = SS_FORMAT_SELL): the caller has turned the quad's padding
+// into -1 (sell_edges), and the real semiring multiplies the gathered value by
+// the slot's matrix value v.
+template <int SR, int FMT>
 __device__ __forceinline__ void scan_quad(const Dev& d, const unsigned* sm, int sbits,
-                                          const unsigned* gbm, int4 c, int first[4], float sum[4],
+                                          const unsigned* gbm, int4 c, int4 v, int first[4], float sum[4],
                                           unsigned live, const float* smf, int sf) {
   const int cc[4] = {c.x, c.y, c.z, c.w};
+  const int vv[4] = {v.x, v.y, v.z, v.w};
   unsigned hit[4];
 #pragma unroll
   for (int r = 0; r < 4; ++r) hit[r] = frontier_bit(sm, sbits, gbm, cc[r]);
@@ -260,7 +282,10 @@ __device__ __forceinline__ void scan_quad(const Dev& d, const unsigned* sm, int 
     if (m) {
 #pragma unroll
       for (int r = 0; r < 4; ++r)
-        if (m >> r & 1u) sum[r] += (cc[r] < sf) ? smf[cc[r]] : __ldg(d.fr + cc[r]);
+        if (m >> r & 1u) {
+          const float x = (cc[r] < sf) ? smf[cc[r]] : __ldg(d.fr + cc[r]);
+          sum[r] += (FMT == SS_FORMAT_SELL) ? __int_as_float(vv[r]) * x : x;
+        }
     }
   }
 }
@@ -271,11 +296,12 @@ extern __shared__ __align__(16) unsigned ss_smem_bits[];
 // Warp w of the grid owns items w, w + W, w + 2W, ... (W = warps in the grid,
 // the item list is ordered for that assignment); it reads the descriptors and
 // SlimWork states of 32 of them at once (one per lane) and walks the active ones.
-template <int SR, int C, int MODE>
+template <int SR, int C, int MODE, int FMT>
 __global__ void __launch_bounds__(PULL_THREADS, 1) k_pull(Dev d, int variant,
                                                           cudaGraphConditionalHandle cond,
                                                           int use_cond) {
-  constexpr int PULL_STEP = pull_step<SR>();
+  constexpr int PULL_STEP = pull_step<SR, FMT>();
+  const int* colp = (FMT == SS_FORMAT_SELL) ? d.scol : d.col;
   constexpr int Q = C / 4;
   if (d.ctl->done) return;
   const int k = d.ctl->k;
@@ -366,14 +392,23 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_pull(Dev d, int variant,
                             (L[2] == SS_INF ? 4u : 0u) | (L[3] == SS_INF ? 8u : 0u);
       int first[4] = {-1, -1, -1, -1};
       float sum[4] = {0.f, 0.f, 0.f, 0.f};
-      const int4* base = reinterpret_cast<const int4*>(d.col + start) + lq;
-      int4 c[SHORT_COLS];
+      const int4* base = reinterpret_cast<const int4*>(colp + start) + lq;
+      const int4* vbase = reinterpret_cast<const int4*>(d.sval + start) + lq;  // (Sell only)
+      int4 c[SHORT_COLS], v[SHORT_COLS];
 #pragma unroll
-      for (int u = 0; u < SHORT_COLS; ++u)
+      for (int u = 0; u < SHORT_COLS; ++u) {
         c[u] = (u < ncols) ? ld_stream(base + u * Q) : make_int4(-1, -1, -1, -1);
+        if (FMT == SS_FORMAT_SELL) {
+          const int4 vq = (u < ncols) ? ld_stream(vbase + u * Q) : make_int4(0, 0, 0, 0);
+          c[u] = sell_edges<SR>(c[u], vq);
+          v[u] = SR == SS_REAL ? vq : make_int4(0, 0, 0, 0);
+        } else {
+          v[u] = make_int4(0, 0, 0, 0);
+        }
+      }
 #pragma unroll
       for (int u = 0; u < SHORT_COLS; ++u)
-        if (u < ncols) scan_quad<SR>(d, sm, sbits, gbm, c[u], first, sum, live, smf, sf);
+        if (u < ncols) scan_quad<SR, FMT>(d, sm, sbits, gbm, c[u], v[u], first, sum, live, smf, sf);
       if (own && lq == 0) {
         cnt.act += 1;
         if (MODE != MODE_FILTERED) cnt.slots += (unsigned long long)ncols * C;
@@ -397,13 +432,13 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_pull(Dev d, int variant,
       if (lane == src) {
         const unsigned bytes = (unsigned)(item.z - item.y) * C * 4u;
         if (bytes > 2048u)
-          prefetch_l2(d.col + start + 512, min(bytes - 2048u, (unsigned)PREFETCH_BYTES));
+          prefetch_l2(colp + start + 512, min(bytes - 2048u, (unsigned)PREFETCH_BYTES));
       }
       if (todo) {
         const int nxt = __ffs(todo) - 1;
         if (lane == nxt) {
           const unsigned bytes = (unsigned)(my_item.z - my_item.y) * C * 4u;
-          prefetch_l2(d.col + my_start, min(bytes, (unsigned)PREFETCH_BYTES));
+          prefetch_l2(colp + my_start, min(bytes, (unsigned)PREFETCH_BYTES));
         }
       }
       // levels of this lane's 4 rows (prefetched; only this chunk's post writes them)
@@ -420,7 +455,8 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_pull(Dev d, int variant,
         for (int r = 0; r < 4; ++r) need |= (L[r] == SS_INF);
       }
       const int nq = (item.z - item.y) * Q;
-      const int4* base = reinterpret_cast<const int4*>(d.col + start);
+      const int4* base = reinterpret_cast<const int4*>(colp + start);
+      const int4* vbase = reinterpret_cast<const int4*>(d.sval + start);  // (Sell only)
       for (int q0 = 0; q0 < nq; q0 += 32 * PULL_STEP) {
         if (MODE == MODE_FILTERED) {
           if (!__any_sync(SS_FULL_MASK, need)) break;
@@ -430,20 +466,31 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_pull(Dev d, int variant,
         if (lane == 0) {
           const long long ahead = (long long)(q0 + 32 * PULL_STEP) * 16 + PREFETCH_BYTES;
           const long long total = (long long)nq * 16;
-          if (ahead < total)
+          if (ahead < total) {
             prefetch_l2(reinterpret_cast<const char*>(base) + ahead,
                         (unsigned)min(total - ahead, (long long)(32 * PULL_STEP * 16)));
+            if (FMT == SS_FORMAT_SELL)
+              prefetch_l2(reinterpret_cast<const char*>(vbase) + ahead,
+                          (unsigned)min(total - ahead, (long long)(32 * PULL_STEP * 16)));
+          }
         }
-        int4 c[PULL_STEP];
+        int4 c[PULL_STEP], v[PULL_STEP];
 #pragma unroll
         for (int u = 0; u < PULL_STEP; ++u) {
           const int q = q0 + lane + 32 * u;
           c[u] = (q < nq) ? ld_stream(base + q) : make_int4(-1, -1, -1, -1);
+          if (FMT == SS_FORMAT_SELL) {
+            const int4 vq = (q < nq) ? ld_stream(vbase + q) : make_int4(0, 0, 0, 0);
+            c[u] = sell_edges<SR>(c[u], vq);
+            v[u] = SR == SS_REAL ? vq : make_int4(0, 0, 0, 0);
+          } else {
+            v[u] = make_int4(0, 0, 0, 0);
+          }
           if (MODE == MODE_FILTERED && q < nq) lane_slots += 4;
         }
 #pragma unroll
-        for (int u = 0; u < PULL_STEP; ++u)
-          if (q0 + 32 * u < nq) scan_quad<SR>(d, sm, sbits, gbm, c[u], first, sum, live, smf, sf);  // warp-uniform
+        for (int u = 0; u < PULL_STEP; ++u)  // (q0 + 32 u < nq is warp-uniform)
+          if (q0 + 32 * u < nq) scan_quad<SR, FMT>(d, sm, sbits, gbm, c[u], v[u], first, sum, live, smf, sf);
         if (MODE == MODE_FILTERED) {  // a row is done once visited or (not real) hit
           need = false;
 #pragma unroll
@@ -662,37 +709,45 @@ int vertex_grid(const slimsell_graph* h, int threads) {
   return (int)std::max(1LL, std::min((long long)8 * h->num_sms, want));
 }
 
-template <int SR, int C, int MODE>
+template <int SR, int C, int MODE, int FMT>
 static ss_status launch_pull(const slimsell_graph* h, const Dev& d, const IterLaunch& il,
                              cudaStream_t st) {
   static std::atomic<unsigned long long> configured{0};
   if (first_on_device(configured))
-    SS_CUDA(cudaFuncSetAttribute(k_pull<SR, C, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    SS_CUDA(cudaFuncSetAttribute(k_pull<SR, C, MODE, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  SS_SMEM_LIMIT_BYTES));
-  k_pull<SR, C, MODE><<<pull_grid(h), PULL_THREADS, (size_t)(d.smem_words + SMEM_GUARD) * 4, st>>>(
+  k_pull<SR, C, MODE, FMT><<<pull_grid(h), PULL_THREADS, (size_t)(d.smem_words + SMEM_GUARD) * 4, st>>>(
       d, il.variant, il.cond, il.use_cond);
   SS_CUDA(cudaGetLastError());
   return SS_OK;
 }
 
-template <int SR, int MODE>
+template <int SR, int MODE, int FMT>
 static ss_status launch_pull_c(const slimsell_graph* h, const Dev& d, const IterLaunch& il,
                                cudaStream_t st) {
   switch (h->C) {
-    case 8: return launch_pull<SR, 8, MODE>(h, d, il, st);
-    case 16: return launch_pull<SR, 16, MODE>(h, d, il, st);
-    case 32: return launch_pull<SR, 32, MODE>(h, d, il, st);
-    default: return launch_pull<SR, 64, MODE>(h, d, il, st);
+    case 8: return launch_pull<SR, 8, MODE, FMT>(h, d, il, st);
+    case 16: return launch_pull<SR, 16, MODE, FMT>(h, d, il, st);
+    case 32: return launch_pull<SR, 32, MODE, FMT>(h, d, il, st);
+    default: return launch_pull<SR, 64, MODE, FMT>(h, d, il, st);
   }
 }
 
+// The Sell-C-sigma format is instantiated for the full and SlimWork passes only
+// (slimsell_bfs accepts it with those policies).
 template <int SR>
 static ss_status launch_pull_m(const slimsell_graph* h, const Dev& d, int mode, const IterLaunch& il,
                                cudaStream_t st) {
+  const bool sell = d.format == SS_FORMAT_SELL;
   switch (mode) {
-    case MODE_FULL: return launch_pull_c<SR, MODE_FULL>(h, d, il, st);
-    case MODE_SLIMWORK: return launch_pull_c<SR, MODE_SLIMWORK>(h, d, il, st);
-    default: return launch_pull_c<SR, MODE_FILTERED>(h, d, il, st);
+    case MODE_FULL:
+      return sell ? launch_pull_c<SR, MODE_FULL, SS_FORMAT_SELL>(h, d, il, st)
+                  : launch_pull_c<SR, MODE_FULL, SS_FORMAT_SLIMSELL>(h, d, il, st);
+    case MODE_SLIMWORK:
+      return sell ? launch_pull_c<SR, MODE_SLIMWORK, SS_FORMAT_SELL>(h, d, il, st)
+                  : launch_pull_c<SR, MODE_SLIMWORK, SS_FORMAT_SLIMSELL>(h, d, il, st);
+    default:
+      return launch_pull_c<SR, MODE_FILTERED, SS_FORMAT_SLIMSELL>(h, d, il, st);
   }
 }
 
@@ -891,8 +946,22 @@ ss_status slimsell_bfs(slimsell_handle h, int32_t root, int32_t semiring, int32_
     set_error("slimsell_bfs: unknown policy %d", policy);
     return SS_ERR_INVALID;
   }
+  if (h->format == SS_FORMAT_SELL && policy != SS_V_FULL && policy != SS_V_SLIMWORK) {
+    set_error("slimsell_bfs: the Sell-C-sigma format runs the FULL and SLIMWORK policies only");
+    return SS_ERR_UNSUPPORTED;
+  }
   cudaStream_t st = (cudaStream_t)stream;
-  const Dev d = h->dev();
+  if (h->format == SS_FORMAT_SELL && !h->sell_col) {
+    if (h->pending) SS_CUDA(cudaEventSynchronize(h->ev_done));
+    ss_status s = sell_arrays(h, st);
+    if (s != SS_OK) return s;
+  }
+  Dev d = h->dev();
+  if (h->format == SS_FORMAT_SELL) {
+    d.format = SS_FORMAT_SELL;
+    d.scol = h->sell_col;
+    d.sval = semiring == SS_TROPICAL ? h->sell_vtrop : h->sell_vmul;
+  }
   const int grid = vertex_grid(h, 256);
   const bool prof = h->profiling != 0;
   const bool device_loop = h->device_loop && !prof;
@@ -1060,6 +1129,14 @@ ss_status slimsell_set_option(slimsell_handle h, int32_t option, int64_t value) 
       return SS_OK;
     case SS_OPT_PROFILE_QUEUE:
       h->profile_queue = value ? 1 : 0;
+      return SS_OK;
+    case SS_OPT_FORMAT:
+      if (value != SS_FORMAT_SLIMSELL && value != SS_FORMAT_SELL) {
+        ss::set_error("slimsell_set_option: format must be SS_FORMAT_SLIMSELL or SS_FORMAT_SELL");
+        return SS_ERR_INVALID;
+      }
+      h->format = (int)value;
+      ss::drop_loop_graphs(h);  // captured loops hold the previous kernels
       return SS_OK;
     case SS_OPT_PUSH_BLOCKS:
       if (value < 0 || value > 2) {

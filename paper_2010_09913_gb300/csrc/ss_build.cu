@@ -632,6 +632,7 @@ ss::Dev slimsell_graph::dev() const {
   d.fr = fr; d.par = par; d.xacc = xacc; d.xpar = xpar; d.arrive = arrive;
   d.units = units; d.units_cap = units_cap;
   d.bunits = bunits; d.bunits_cap = bunits_cap; d.push_blocks = push_blocks;
+  d.format = SS_FORMAT_SLIMSELL; d.scol = nullptr; d.sval = nullptr;  // set per call by slimsell_bfs
   d.pbest = pbest; d.psum = psum; d.touched = touched; d.mlp = mlp; d.feats = feats;
   d.sel_margin = sel_margin;
   for (int b = 0; b < 2; ++b) {

@@ -85,6 +85,9 @@ struct Dev {
   const int* cl;        // [n_c] chunk lengths
   const long long* cs;  // [n_c + 1] chunk starts (in slots)
   const int* col;       // [slots] SlimSell column array (-1 = padding)
+  int format;           // SS_FORMAT_SLIMSELL, or SS_FORMAT_SELL: the pull streams scol and sval
+  const int* scol;      // [slots] Sell-C-sigma column array (padding 0), when format is Sell
+  const float* sval;    // [slots] Sell-C-sigma values of the run's semiring (1 edge, its zero padding)
   const int4* items;    // [n_items] (chunk, j0, j1, split index or -1)
   const int* split_n;   // [n_split] items per split chunk
   int* lvl;             // [n_pad] level (SS_INF = unvisited); the tropical f vector
@@ -204,6 +207,10 @@ struct slimsell_graph {
   int pending = 0;                     // last-run statistics not yet read back
   int device_loop = 1;                 // iterate with a conditional CUDA graph
   int profile_queue = 1;               // host-driven fixed variants: queue iterations in batches
+  int format = SS_FORMAT_SLIMSELL;     // storage format the pull streams (SS_OPT_FORMAT)
+  const int* sell_col = nullptr;       // Sell-C-sigma arrays, built on first use (ss_sell.cu)
+  const float* sell_vtrop = nullptr;
+  const float* sell_vmul = nullptr;
   cudaGraphExec_t loop_exec[4][6] = {};  // [semiring][policy] device-side iteration loops
   int loop_smem_words[4][6] = {};
   std::vector<int> iter_ns;            // per-iteration kernel time of the last profiled call

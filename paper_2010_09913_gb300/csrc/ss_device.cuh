@@ -272,6 +272,9 @@ ss_status multi_start(slimsell_graph* h, const int32_t* d_roots, int k, cudaStre
 ss_status multi_level(slimsell_graph* h, const MultiDev& m, int W, cudaStream_t st, bool* done,
                       cudaEvent_t before = nullptr, cudaEvent_t after = nullptr);
 
+// The handle's Sell-C-sigma arrays, built on first use (ss_sell.cu).
+ss_status sell_arrays(slimsell_graph* h, cudaStream_t st);
+
 __global__ void k_init(Dev d);
 
 // Grid sizes that follow the graph size (ss_bfs.cu).

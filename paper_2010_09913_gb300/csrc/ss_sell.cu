@@ -204,6 +204,22 @@ ss_status ab_scratch(slimsell_graph* h, bool sell, cudaStream_t st, AbScratch** 
   return SS_OK;
 }
 
+}  // namespace
+
+// The Sell-C-sigma arrays of the handle (built on first use), for the
+// production pull's format option.
+ss_status sell_arrays(slimsell_graph* h, cudaStream_t st) {
+  AbScratch* a = nullptr;
+  ss_status s = ab_scratch(h, true, st, &a);
+  if (s != SS_OK) return s;
+  h->sell_col = a->scol;
+  h->sell_vtrop = a->vtrop;
+  h->sell_vmul = a->vmul;
+  return SS_OK;
+}
+
+namespace {
+
 template <int SR>
 ss_status run_ab(slimsell_graph* h, int root, int format, int* d_dist, double* kernel_ms,
                  cudaStream_t st) {

@@ -295,3 +295,29 @@ def test_push_block_sparse_frontier(blocks):
             G.set_option(ss.OPT_PUSH_BLOCKS, 3)
         finally:
             G.close()
+
+
+def test_sell_format_in_the_production_pull():
+    """The pull over the Sell-C-sigma arrays (explicit values, padding column 0
+    with the semiring's zero) gives the oracle's distances and parents for every
+    semiring, C and sigma with the full and SlimWork passes; other policies are
+    refused with that format, and switching back restores SlimSell."""
+    for g in [gg.kronecker(12, seed=3), gg.lattice(33, 0.05, seed=2), gg.from_edges(5, [(0, 1), (3, 4)])]:
+        for C, sigma, split_w in [(32, 0, 64), (8, 1, 4), (64, 128, 0), (16, 1, 16)]:
+            G = ss.SlimSellGraph.from_host(g.row_ptr, g.col, C=C, sigma=sigma or g.n, split_w=split_w)
+            G.set_option(ss.OPT_FORMAT, ss.FORMAT_SELL)
+            for r in gg.roots(g, 2, seed=6):
+                d, p = expected(g, r)
+                for sr in SEMIRINGS:
+                    for pol in ("slimwork", "full"):
+                        dist, parent = run(G, r, sr, pol)
+                        np.testing.assert_array_equal(dist, d, err_msg=f"{g.name} C={C} {sr} {pol}")
+                        np.testing.assert_array_equal(parent, p, err_msg=f"{g.name} C={C} {sr} {pol}")
+            with pytest.raises(ss.SlimSellError):
+                run(G, int(gg.roots(g, 1, seed=6)[0]), "tropical", "heuristic")
+            G.set_option(ss.OPT_FORMAT, ss.FORMAT_SLIMSELL)
+            r = int(gg.roots(g, 1, seed=6)[0])
+            d, p = expected(g, r)
+            dist, parent = run(G, r, "selmax", "heuristic")
+            np.testing.assert_array_equal(dist, d)
+            G.close()
