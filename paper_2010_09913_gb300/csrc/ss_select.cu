@@ -58,7 +58,12 @@ __global__ void __launch_bounds__(DECIDE_THREADS) k_decide(Dev d, int policy, cu
   __shared__ int choice, stop;
   Ctl* c = d.ctl;
   const int t = threadIdx.x;
-  if (policy == SS_V_LEARNED && d.mlp != nullptr)  // in flight while thread 0 computes the features
+  // a frontier the cluster push takes stays with it (that launch runs the
+  // following small levels too, a saving no per-level time can express), so the
+  // network is evaluated only on levels that need a grid-wide pass; elsewhere the
+  // learned policy takes the frontier-size rule's choice, the cluster push
+  const bool net = policy == SS_V_LEARNED && d.mlp != nullptr && !local_fits(d, c->prev_new, c->prev_deg);
+  if (net)  // in flight while thread 0 computes the features
     for (int i = t; i < N_PARAMS / 4; i += DECIDE_THREADS)
       reinterpret_cast<float4*>(wsh)[i] = __ldg(reinterpret_cast<const float4*>(d.mlp) + i);
   if (t == 0) {
@@ -94,7 +99,7 @@ __global__ void __launch_bounds__(DECIDE_THREADS) k_decide(Dev d, int policy, cu
     choice = v;
   }
   __syncthreads();
-  if (policy == SS_V_LEARNED && d.mlp != nullptr) {
+  if (net) {
     const float* W = wsh;
     float a = 0.f;
     if (t < F_H) {
@@ -126,10 +131,6 @@ __global__ void __launch_bounds__(DECIDE_THREADS) k_decide(Dev d, int policy, cu
       int hv = choice;
       if (hv == VAR_PUSH && !push_fits(d, c)) hv = VAR_FILTERED;
       if (d.sel_margin > 0.0f && y[best] + d.sel_margin >= y[hv]) best = hv;
-      // a frontier the cluster push takes stays with it: that launch runs the
-      // following small levels too, a saving no per-level time can express, so
-      // the network only chooses among levels that need a grid-wide pass
-      if (local_fits(d, c->prev_new, c->prev_deg)) best = VAR_PUSH;
       choice = best;
     }
     __syncthreads();
