@@ -160,6 +160,24 @@ ss_status slimsell_bfs(slimsell_handle h, int32_t root, int32_t semiring, int32_
                        int32_t* d_dist, int32_t* d_parent, void* stream);
 
 /*
+ * The real-semiring frontier values of the handle's last slimsell_bfs call
+ * (Section III-A: over (R, +, *, 0, 1) the frontier keeps x_k on the rows it
+ * adds, and x_k sums the values of a row's neighbours in f_{k-1}; starting
+ * from f_0 = e_root that is the number of shortest root-v paths).
+ *   d_out  float[n] device, written in original vertex order: the value v
+ *          entered the frontier with (1 for the root), 0 where the run did not
+ *          reach.  fp32 sums in no fixed order, so exact while a count stays
+ *          below 2^24.
+ * Queued on `stream`; order it after the BFS call's work when that ran on
+ * another stream.
+ * Errors: SS_ERR_INVALID (NULL arguments, or the handle's last run was not a
+ * real-semiring slimsell_bfs: any other run on the handle, a multi-source,
+ * betweenness, format-comparison or batch call included, replaces the values),
+ * SS_ERR_CUDA.
+ */
+ss_status slimsell_get_values(slimsell_handle h, float* d_out, void* stream);
+
+/*
  * Multi-source BFS (an extension beyond the paper): the boolean semiring of
  * Section III-A run for k sources at once, frontiers bit-packed as
  * ceil(k / 64) uint64 words per vertex, rounded up to a power of two and to at

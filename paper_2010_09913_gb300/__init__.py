@@ -83,6 +83,7 @@ def lib():
     sigs = {
         "slimsell_build": (i32, [_VP, _VP, i32, i64, i32, i32, i32, _VP, ctypes.POINTER(_VP)]),
         "slimsell_bfs": (i32, [_VP, i32, i32, i32, _VP, _VP, _VP]),
+        "slimsell_get_values": (i32, [_VP, _VP, _VP]),
         "slimsell_bfs_multi": (i32, [_VP, _VP, i32, i32, _VP, _VP]),
         "slimsell_bfs_multi_parents": (i32, [_VP, _VP, i32, i32, _VP, _VP, _VP]),
         "slimsell_bfs_spmv": (i32, [_VP, i32, i32, i32, _VP, ctypes.POINTER(ctypes.c_double), _VP]),
@@ -121,7 +122,7 @@ def lib():
 
 def exported_symbols() -> list[str]:
     return ["slimsell_build", "slimsell_bfs", "slimsell_bfs_multi", "slimsell_bfs_multi_parents",
-            "slimsell_bfs_spmv", "slimsell_bc",
+            "slimsell_bfs_spmv", "slimsell_bc", "slimsell_get_values",
             "slimsell_get_info", "slimsell_get_run_stats",
             "slimsell_set_profiling", "slimsell_set_option", "slimsell_export_layout",
             "slimsell_destroy",
@@ -167,6 +168,11 @@ def slimsell_bfs(h: int, root: int, semiring: int, policy: int, dist: torch.Tens
     _check("slimsell_bfs", lib().slimsell_bfs(
         h, int(root), int(semiring), int(policy), _ptr(dist, torch.int32, "dist"),
         _ptr(parent, torch.int32, "parent"), _stream(stream)))
+
+
+def slimsell_get_values(h: int, out: torch.Tensor, stream=None) -> None:
+    _check("slimsell_get_values", lib().slimsell_get_values(h, _ptr(out, torch.float32, "out"),
+                                                            _stream(stream)))
 
 
 def slimsell_bfs_multi(h: int, roots: torch.Tensor, policy: int, dist: torch.Tensor | None,
@@ -401,6 +407,13 @@ class SlimSellGraph:
             parent = torch.empty(self.n, dtype=torch.int32, device=dev)
         slimsell_bfs(self.h, root, sr, pol, dist, parent, stream)
         return dist, parent
+
+    def values(self, out=None, stream=None):
+        """Path counts of the last real-semiring bfs() (float32, original vertex order)."""
+        if out is None:
+            out = torch.empty(self.n, dtype=torch.float32, device=torch.device("cuda", torch.cuda.current_device()))
+        slimsell_get_values(self.h, out, stream)
+        return out
 
     def bfs_multi(self, roots, policy="slimwork", dist=None, want_dist: bool = True, stream=None):
         """k-source BFS; returns dist as an (n, k) int32 tensor (vertex-major)."""

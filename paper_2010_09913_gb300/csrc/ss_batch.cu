@@ -141,6 +141,7 @@ ss_status slimsell_batch_run(slimsell_batch_handle b, const int32_t* d_roots,
   }
   const int g = (int)b->hs.size();
   cudaStream_t st = (cudaStream_t)stream;
+  for (slimsell_handle hg : b->hs) hg->values_semiring = -1;
   if (b->pending) SS_CUDA(cudaEventSynchronize(b->done));
   std::vector<int> roots((size_t)g);
   SS_CUDA(cudaMemcpyAsync(roots.data(), d_roots, sizeof(int) * (size_t)g, cudaMemcpyDeviceToHost, st));

@@ -199,6 +199,7 @@ extern "C" ss_status slimsell_bc(slimsell_handle h, const int32_t* d_sources, in
     set_error("slimsell_bc: NULL argument");
     return SS_ERR_INVALID;
   }
+  h->values_semiring = -1;
   if (k < 1) {
     set_error("slimsell_bc: k must be at least 1 (got %d)", k);
     return SS_ERR_INVALID;

@@ -205,6 +205,7 @@ struct slimsell_graph {
   cudaEvent_t ev_a = nullptr, ev_b = nullptr, ev_c = nullptr, ev_d = nullptr;
   cudaEvent_t ev_done = nullptr;       // end of the last call's work on its stream
   int pending = 0;                     // last-run statistics not yet read back
+  int values_semiring = -1;            // semiring of the slimsell_bfs call whose values fr holds (-1: none)
   int device_loop = 1;                 // iterate with a conditional CUDA graph
   int profile_queue = 1;               // host-driven fixed variants: queue iterations in batches
   int format = SS_FORMAT_SLIMSELL;     // storage format the pull streams (SS_OPT_FORMAT)

@@ -539,6 +539,7 @@ extern "C" ss_status slimsell_bfs_multi_parents(slimsell_handle h, const int32_t
     set_error("slimsell_bfs_multi: NULL argument");
     return SS_ERR_INVALID;
   }
+  h->values_semiring = -1;
   if (k < 1 || k > 1024) {
     set_error("slimsell_bfs_multi: k must be in [1, 1024] (got %d)", k);
     return SS_ERR_INVALID;

@@ -290,6 +290,7 @@ extern "C" ss_status slimsell_bfs_spmv(slimsell_handle h, int32_t root, int32_t 
     set_error("slimsell_bfs_spmv: NULL argument");
     return SS_ERR_INVALID;
   }
+  h->values_semiring = -1;
   if (root < 0 || root >= h->n) {
     set_error("slimsell_bfs_spmv: root %d out of range [0, %d)", root, h->n);
     return SS_ERR_INVALID;

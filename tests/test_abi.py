@@ -78,4 +78,6 @@ def test_extension_entry_points_reject_null_on_host(lib):
     assert lib.slimsell_bc(None, fake, 1, fake, None, None) == 1
     assert lib.slimsell_bc(fake, None, 1, fake, None, None) == 1
     assert lib.slimsell_bc(fake, fake, 1, None, None, None) == 1
+    assert lib.slimsell_get_values(None, fake, None) == 1
+    assert lib.slimsell_get_values(fake, None, None) == 1
     assert "NULL" in ss.slimsell_last_error()
