@@ -267,7 +267,8 @@ __device__ __forceinline__ void carry_chunk(const Dev& d, int k, int chunk, int 
 //
 // Sell-C-sigma (FMT = SS_FORMAT_SELL): the caller has turned the quad's padding
 // into -1 (sell_edges), and the real semiring multiplies the gathered value by
-// the slot's matrix value v.
+// the slot's matrix value v.  The real semiring over SlimSell takes quad_hits
+// and gather_step instead, which gather a whole step's values at once.
 template <int SR, int FMT>
 __device__ __forceinline__ void scan_quad(const Dev& d, const unsigned* sm, int sbits,
                                           const unsigned* gbm, int4 c, int4 v, int first[4], float sum[4],
@@ -290,6 +291,50 @@ __device__ __forceinline__ void scan_quad(const Dev& d, const unsigned* sm, int 
         }
     }
   }
+}
+
+
+// Real semiring, SlimSell: the frontier hits of one quad (bit r for row r) and
+// the first-hit update; the value gathers follow for the whole step at once.
+__device__ __forceinline__ unsigned quad_hits(const unsigned* sm, int sbits, const unsigned* gbm, int4 c,
+                                              int first[4]) {
+  const int cc[4] = {c.x, c.y, c.z, c.w};
+  unsigned m = 0;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const unsigned h = frontier_bit(sm, sbits, gbm, cc[r]);
+    first[r] = (h && first[r] < 0) ? cc[r] : first[r];
+    m |= h << r;
+  }
+  return m;
+}
+
+// Gather and add the values of every live hit of a step's U quads: all loads are
+// issued before the first add, so a warp waits once per step, not once per quad
+// (Kronecker 22 hub level: 322 -> 278 us; the gathers are latency-bound, and
+// staging more hub rows as 8- or 16-bit counts measured no faster).
+template <int U>
+__device__ __forceinline__ void gather_step(const Dev& d, const int4* c, const unsigned* mm, float sum[4],
+                                            const float* smf, int sf) {
+  unsigned any = 0;
+#pragma unroll
+  for (int u = 0; u < U; ++u) any |= mm[u];
+  if (!any) return;
+  float x[U][4];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int cc[4] = {c[u].x, c[u].y, c[u].z, c[u].w};
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      float v = 0.f;
+      if (mm[u] >> r & 1u) v = (cc[r] < sf) ? smf[cc[r]] : __ldg(d.fr + cc[r]);
+      x[u][r] = v;
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) sum[r] += x[u][r];
 }
 
 extern __shared__ __align__(16) unsigned ss_smem_bits[];
@@ -408,9 +453,17 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_pull(Dev d, int variant,
           v[u] = make_int4(0, 0, 0, 0);
         }
       }
+      if constexpr (SR == SS_REAL && FMT == SS_FORMAT_SLIMSELL) {
+        unsigned mm[SHORT_COLS];
 #pragma unroll
-      for (int u = 0; u < SHORT_COLS; ++u)
-        if (u < ncols) scan_quad<SR, FMT>(d, sm, sbits, gbm, c[u], v[u], first, sum, live, smf, sf);
+        for (int u = 0; u < SHORT_COLS; ++u)
+          mm[u] = (u < ncols) ? quad_hits(sm, sbits, gbm, c[u], first) & live : 0u;
+        gather_step<SHORT_COLS>(d, c, mm, sum, smf, sf);
+      } else {
+#pragma unroll
+        for (int u = 0; u < SHORT_COLS; ++u)
+          if (u < ncols) scan_quad<SR, FMT>(d, sm, sbits, gbm, c[u], v[u], first, sum, live, smf, sf);
+      }
       if (own && lq == 0) {
         cnt.act += 1;
         if (MODE != MODE_FILTERED) cnt.slots += (unsigned long long)ncols * C;
@@ -490,9 +543,17 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_pull(Dev d, int variant,
           }
           if (MODE == MODE_FILTERED && q < nq) lane_slots += 4;
         }
+        if constexpr (SR == SS_REAL && FMT == SS_FORMAT_SLIMSELL) {
+          unsigned mm[PULL_STEP];
 #pragma unroll
-        for (int u = 0; u < PULL_STEP; ++u)  // (q0 + 32 u < nq is warp-uniform)
-          if (q0 + 32 * u < nq) scan_quad<SR, FMT>(d, sm, sbits, gbm, c[u], v[u], first, sum, live, smf, sf);
+          for (int u = 0; u < PULL_STEP; ++u)
+            mm[u] = (q0 + 32 * u < nq) ? quad_hits(sm, sbits, gbm, c[u], first) & live : 0u;
+          gather_step<PULL_STEP>(d, c, mm, sum, smf, sf);
+        } else {
+#pragma unroll
+          for (int u = 0; u < PULL_STEP; ++u)  // (q0 + 32 u < nq is warp-uniform)
+            if (q0 + 32 * u < nq) scan_quad<SR, FMT>(d, sm, sbits, gbm, c[u], v[u], first, sum, live, smf, sf);
+        }
         if (MODE == MODE_FILTERED) {  // a row is done once visited or (not real) hit
           need = false;
 #pragma unroll
