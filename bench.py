@@ -329,7 +329,8 @@ def train_selector(ss, torch, g, h, args):
     X, T, M = selector.collect(G, gg.roots(g, 64, seed=99), "tropical", repeats=2, max_per_root=24)
     Xs.append(X); Ts.append(T); Ms.append(M)
     for tg, nr in ((gg.kronecker(14, seed=7), 8), (gg.kronecker(18, seed=7), 16),
-                   (gg.lattice(4096, 0.05, seed=7), 1), (gg.erdos_renyi(1 << 22, 16.0, seed=7), 8)):
+                   (gg.kronecker(23, seed=7), 8), (gg.lattice(4096, 0.05, seed=7), 1),
+                   (gg.erdos_renyi(1 << 22, 16.0, seed=7), 8)):
         G = ss.SlimSellGraph.from_host(tg.row_ptr, tg.col, C=32, sigma=tg.n, split_w=args.split_w)
         X, T, M = selector.collect(G, gg.roots(tg, nr, seed=8), "tropical", repeats=2, max_per_root=24)
         Xs.append(X); Ts.append(T); Ms.append(M)
@@ -338,8 +339,8 @@ def train_selector(ss, torch, g, h, args):
                              lr=1e-3)
     return w, {"samples": int(sum(x.shape[0] for x in Xs)), "final_loss": loss,
                "seconds": time.perf_counter() - t0, "margin_log_units": SELECTOR_MARGIN / 1000.0,
-               "graphs": f"kronecker {args.scale} (64 roots other than the timed ones), kronecker 14 "
-                         "and 18, lattice 4096^2 (5% deleted, seed 7), ER 2^22 (mean deg 16, seed 7)"}
+               "graphs": f"kronecker {args.scale} (64 roots other than the timed ones), kronecker 14, 18 "
+                         "and 23, lattice 4096^2 (5% deleted, seed 7), ER 2^22 (mean deg 16, seed 7)"}
 
 
 def batched_learned(ss, torch, g, h, roots, args, stream, dev, runs_edges):
