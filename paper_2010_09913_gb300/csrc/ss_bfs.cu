@@ -1049,7 +1049,9 @@ ss_status slimsell_bfs(slimsell_handle h, int32_t root, int32_t semiring, int32_
   const int grid = vertex_grid(h, 256);
   const bool prof = h->profiling != 0;
   const bool device_loop = h->device_loop && !prof;
-  if (h->pending) SS_CUDA(cudaEventSynchronize(h->ev_done));  // statistics of the previous call
+  // the previous call's statistics are dropped without waiting for it: its work is
+  // ahead of this call's on the same stream (the handle's contract), and a host
+  // wait here left the GPU idle between back-to-back runs
   h->pending = 0;
   h->iter_ns.clear();
   double iter_ms = 0.0;
@@ -1222,6 +1224,8 @@ ss_status slimsell_set_option(slimsell_handle h, int32_t option, int64_t value) 
     ss::set_error("slimsell_set_option: NULL handle");
     return SS_ERR_INVALID;
   }
+  // options change captured loops and buffers a queued run may still be using
+  if (h->pending) SS_CUDA(cudaEventSynchronize(h->ev_done));
   switch (option) {
     case SS_OPT_DP_PASS:
       h->dp_pass = value ? 1 : 0;

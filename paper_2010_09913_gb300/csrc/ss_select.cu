@@ -307,6 +307,7 @@ ss_status slimsell_selector_load(slimsell_handle h, const float* h_weights, int6
     ss::set_error("slimsell_selector_load: NULL handle");
     return SS_ERR_INVALID;
   }
+  if (h->pending) SS_CUDA(cudaEventSynchronize(h->ev_done));  // a queued run may read the weights
   if (!h_weights) {  // unload: the learned policy falls back to the heuristic
     ss::drop_loop_graphs(h);  // captured loops hold the weight pointer
     if (h->mlp) cudaFree(h->mlp);
