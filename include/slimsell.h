@@ -153,7 +153,9 @@ ss_status slimsell_build(const int64_t* d_row_ptr, const int32_t* d_col, int32_t
  * returns after the BFS has finished.
  * The outputs, and the handle's state, belong to this call until `stream`
  * reaches its end: do not start another call on the same handle from a
- * different stream before that.
+ * different stream before that.  Calls on the same stream queue behind one
+ * another without a host wait (the previous call's statistics are dropped);
+ * slimsell_set_option and slimsell_selector_load wait for a queued run first.
  * Errors: SS_ERR_INVALID, SS_ERR_CUDA, SS_ERR_UNSUPPORTED.
  */
 ss_status slimsell_bfs(slimsell_handle h, int32_t root, int32_t semiring, int32_t policy,
